@@ -1,0 +1,221 @@
+/*
+ * ann.h -- C ABI of the GB300 graph-search library (libann.so).
+ *
+ * The library answers K-nearest-neighbour queries over a fixed similarity
+ * graph with the best-first search of Speed-ANN (arXiv 2201.13007). The
+ * problem statement it follows is Def. 1 and 2 of Sec. 2.1: given a point set
+ * P of n points in d dimensions (preprocessed once into an index) and a query
+ * q, return the K points of P closest to q. Closeness is the l2 distance
+ * (Sec. 2.1), ranked and reported as its square; inner product (not in the
+ * paper) ranks by key = -<q, x>.
+ *
+ * Conventions for every call:
+ *   - Return value: ANN_OK (0) or a negative ann_status. On failure
+ *     ann_last_error() returns a message for the calling thread.
+ *   - Argument errors are detected on the host before anything is enqueued;
+ *     nothing is written to the outputs then.
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc,
+ *     torch CUDA tensors); "host pointer" means ordinary or pinned host memory.
+ *   - Streams are passed as void* holding a cudaStream_t (NULL = legacy
+ *     default stream). Calls on a stream are asynchronous unless stated.
+ *   - Vertex ids are int32 in the graph and int64 in results; n < 2^31.
+ *   - The total order used for results is (key ascending, id ascending).
+ */
+#ifndef ANN_H
+#define ANN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ANN_OK = 0,
+    ANN_ERR_ARG = -1,     /* invalid argument (shape, range, null pointer) */
+    ANN_ERR_OOM = -2,     /* device or host allocation failed */
+    ANN_ERR_CUDA = -3,    /* a CUDA call failed; the message names it */
+    ANN_ERR_BUSY = -4,    /* serving: no free request slot right now */
+    ANN_ERR_TIMEOUT = -5, /* serving: nothing completed within the wait limit */
+    ANN_ERR_STATE = -6    /* object used in a state that does not allow the call */
+} ann_status;
+
+/* Storage type of the base vectors inside the index. Reduced-precision
+ * storage cuts the bytes gathered per distance; distances are always
+ * accumulated in FP32. */
+typedef enum {
+    ANN_STORE_F32 = 0,
+    ANN_STORE_BF16 = 1,
+    ANN_STORE_F16 = 2,
+    ANN_STORE_E4M3 = 3 /* OCP FP8 E4M3 with one FP32 scale per vector: max|x|/448 */
+} ann_storage;
+
+typedef enum { ANN_METRIC_L2 = 0, ANN_METRIC_IP = 1 } ann_metric;
+
+/* Search modes (Sec. 4):
+ *   ANN_MODE_SYNC  -- bulk-synchronous top-M expansion with the staged
+ *                     schedule (Sec. 4.1, 4.2); deterministic; BFiS
+ *                     (Algorithm 1) is M = 1.
+ *   ANN_MODE_ASYNC -- Algorithm 3: walkers with private queues, a shared
+ *                     visited map updated without ordering, and the
+ *                     update-position merge test of Algorithm 2. */
+typedef enum { ANN_MODE_SYNC = 0, ANN_MODE_ASYNC = 1 } ann_mode;
+
+/* ann_index_create flags */
+#define ANN_INDEX_DEVICE_INPUT 0x1 /* base and adj are device pointers */
+#define ANN_INDEX_KEEP_F32 0x2     /* keep an FP32 copy of the base for re-rank */
+
+typedef struct ann_index ann_index;
+
+typedef struct {
+    int64_t n;
+    int32_t d;
+    int32_t d_pad;       /* row length in elements; rows are padded with zeros to 16 bytes */
+    int32_t R;           /* adjacency row length (degree cap) */
+    int32_t storage;     /* ann_storage */
+    int32_t metric;      /* ann_metric */
+    int32_t has_f32;     /* 1 if an FP32 copy is kept for re-rank */
+    int64_t entry;
+    int64_t device_bytes; /* HBM held by the index */
+} ann_index_info;
+
+/* Per-query counters, written by the search kernels when requested. */
+typedef struct {
+    int64_t steps;        /* BSP steps (sync) or global steps (async) */
+    int64_t expansions;   /* vertices expanded (marked checked) */
+    int64_t evals;        /* distance computations, entry included */
+    int64_t hash_resets;  /* visited-table resets (the table forgets, Sec. 4.4 tolerates re-visits) */
+    int64_t dup_dropped;  /* candidates dropped because their id was already queued */
+    int64_t merges;       /* async: merges of the private queues */
+    int64_t t_start_ns;   /* device globaltimer when the query started */
+    int64_t t_end_ns;     /* device globaltimer when its results were written */
+} ann_query_stats;
+
+/* Optional knobs for ann_search_ex; zero-initialise and set what is needed. */
+typedef struct {
+    int32_t mode;       /* ann_mode; default ANN_MODE_SYNC */
+    int32_t M0;         /* initial expansion width; 0 = 1 (Algorithm 3 starts at M = 1) */
+    int32_t t;          /* sync mode: M doubles every t steps; 0 = 1 (Sec. 4.2 example) */
+    float R_ratio;      /* async: Algorithm 2 position ratio; 0 = 0.8; INFINITY = merge only when idle */
+    int32_t rerank;     /* 1 = recompute the final queue's keys from FP32 rows (needs has_f32) */
+    int32_t threads;    /* threads per CTA: 0 = auto, else 64, 128, 256 or 512 */
+    int32_t hash_bits;  /* log2 slots of the per-query visited table; 0 = auto, else 8..15 */
+    int32_t persistent; /* 1 = persistent grid that pulls queries from a device counter */
+    /* Per-query settings (device int32 arrays of nq entries, or NULL for the
+     * uniform k, L, M arguments). When given, k, L and M passed to the call
+     * are the maxima over the batch, and each entry must lie in [1, max]. */
+    const int32_t *k_per_query;
+    const int32_t *L_per_query;
+    const int32_t *M_per_query;
+    ann_query_stats *stats; /* device array of nq, or NULL */
+} ann_search_params;
+
+/* Build an index (Sec. 2.1: "preprocess P").
+ *   base   n x d float32, row-major (host or device, see flags).
+ *   adj    n x R int32, row-major, entries in [-1, n), -1 = no edge; the
+ *          graph of Sec. 3.1 (stored CSR in the paper, fixed degree here).
+ *   entry  the starting point P of Algorithm 1, in [0, n).
+ *   storage, metric  see the enums; flags ANN_INDEX_*.
+ * The library copies everything into memory it owns; the caller keeps its
+ * buffers. Reduced-precision storage encodes on the device. Errors:
+ * ANN_ERR_ARG for n < 1, n >= 2^31, d not in [1, 4096], R not in [1, 256],
+ * entry out of range or an adjacency id out of range; ANN_ERR_OOM;
+ * ANN_ERR_CUDA. Synchronous: returns when the index is ready. */
+int ann_index_create(const float *base, int64_t n, int32_t d, int32_t storage, const int32_t *adj,
+                     int32_t R, int64_t entry, int32_t metric, int32_t flags, ann_index **out);
+
+/* Free everything the index owns. NULL is a no-op. The caller must not
+ * destroy an index while searches on it are in flight. */
+void ann_index_destroy(ann_index *index);
+
+/* Shape and storage of an index. */
+int ann_index_get_info(const ann_index *index, ann_index_info *info);
+
+/* Search nq queries (Algorithm 1 / Sec. 4.1-4.2 top-M with M doubling from 1,
+ * one CTA per query).
+ *   queries    device, nq x d float32 row-major.
+ *   k          results per query (the paper's K), 1 <= k <= L.
+ *   L          candidate-queue capacity of Algorithm 1, 1 <= L <= 2048.
+ *   M          maximum expansion width (the paper's M, capped by T), 1..64.
+ *   out_ids    device int64 nq x k; out_dists device float nq x k (squared
+ *              l2, or -<q,x>). Slots beyond the reachable set hold (-1, +inf).
+ * Asynchronous on stream; argument errors return before anything is queued.
+ * nq = 0 is a no-op. Equivalent to ann_search_ex with default params. */
+int ann_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
+               int32_t M, int64_t *out_ids, float *out_dists, void *stream);
+
+/* ann_search with the knobs of ann_search_params (mode, schedule, re-rank,
+ * per-query k/L/M, counters). params may be NULL. */
+int ann_search_ex(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
+                  int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
+                  void *stream);
+
+/* The same search from HOST buffers: copies the queries to the device,
+ * searches, copies the results back and synchronises the stream before it
+ * returns. queries host nq x d float32; out_ids / out_dists host nq x k.
+ * Pinned host memory keeps the copies asynchronous to the CPU. The library
+ * keeps device staging buffers per index, grown on demand (the index must
+ * not be used by two host-buffer calls at once). params may be NULL; its
+ * per-query arrays, if any, must be device pointers. */
+int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
+                    int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
+                    void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *ann_last_error(void);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: requests are submitted one at a time from the host
+ * and admitted to the GPU as request slots and device scratch free up; the
+ * library's scheduler thread groups the admitted requests into launches on
+ * several streams so work that arrives while other work is running overlaps
+ * with it on the device. Each request's result is the same as a single
+ * ann_search of that query with the same k, L, M (sync mode). */
+
+typedef struct {
+    int32_t slots;          /* requests admitted at once (device-resident state); 0 = 4096 */
+    int32_t max_batch;      /* queries per launch; 0 = 1024 */
+    int32_t streams;        /* launches in flight; 0 = 4 */
+    int32_t max_k;          /* per-request limits; 0 = 100 / 1024 / 32 */
+    int32_t max_L;
+    int32_t max_M;
+    int32_t mode;           /* ann_mode for every request */
+    int32_t rerank;         /* as in ann_search_params */
+    int64_t scratch_bytes;  /* device bytes for request state; 0 = derived from slots */
+} ann_serve_config;
+
+typedef struct ann_server ann_server;
+
+typedef struct {
+    uint64_t tag;           /* the caller's tag from ann_serve_submit */
+    int32_t k;              /* valid entries in ids / dists */
+    int32_t status;         /* ANN_OK or the request's error */
+    double latency_us;      /* submit to completion, host clock */
+    double device_us;       /* the query's own time on the device */
+} ann_result;
+
+/* Create a server over an index (the index must outlive it). */
+int ann_serve_create(const ann_index *index, const ann_serve_config *cfg, ann_server **out);
+
+/* Drain in-flight work, stop the scheduler and free everything. NULL is a no-op. */
+void ann_serve_destroy(ann_server *server);
+
+/* Submit one query (host pointer, d float32; copied before return) with its
+ * own k, L, M. Returns ANN_ERR_BUSY without blocking when every slot is
+ * taken, ANN_ERR_ARG for limits outside the config. */
+int ann_serve_submit(ann_server *server, const float *query, int32_t k, int32_t L, int32_t M,
+                     uint64_t tag);
+
+/* Collect up to max completed requests. results[i] describes request i;
+ * its ids / dists are written to out_ids + i * cfg.max_k and
+ * out_dists + i * cfg.max_k (host). Waits at most timeout_us microseconds
+ * for the first completion; returns the number collected (>= 0), or
+ * ANN_ERR_TIMEOUT when nothing completed in time. */
+int ann_serve_poll(ann_server *server, ann_result *results, int64_t *out_ids, float *out_dists,
+                   int32_t max, int32_t timeout_us);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANN_H */

@@ -1,0 +1,426 @@
+"""Seeded synthetic workloads: base vectors, queries and the similarity graph.
+
+This module builds the INPUTS of the search and nothing of the search itself:
+Gaussian-mixture point sets shaped like the paper's datasets (Table 3: SIFT1M
+128-d, GIST1M 960-d, DEEP 96-d) and a fixed-degree similarity graph over them.
+Graph construction is not the paper's method (Sec. 2.2 takes a prebuilt NSG
+index and says construction is not its focus), so the builder here is plain
+index preparation: an exact k-NN list, an occlusion prune of the kind NSG uses,
+reverse edges to fill the degree, and a reachability repair from the entry.
+
+Both the CUDA path and the CPU oracle consume what this module returns; it
+imports neither. Every random draw is a numpy PCG64 stream with a fixed seed.
+
+Workload recipes (n x d, components, distribution):
+
+- ``tiny``   10,000 x 32 float32, 16-component mixture, means U[-1,1]^32,
+  isotropic sigma 0.15, equal weights; graph = exact 16-NN (L2, self
+  excluded) + reverse edges by ascending distance, degree cap 24.
+- ``sift``   n x 128 integer-valued (0..255) vectors: 64 components, means
+  U[0,255]^128 * 0.6 + 51, sigma 30, rounded to nearest and clipped to
+  [0, 255]; graph = 64-NN, occlusion prune to 32, reverse fill to 32.
+- ``gist``   n x 960 non-negative: 32 components, x = exp(mu_c + 0.5 z),
+  mu_c ~ N(-2, 0.5)^960; graph as ``sift``.
+- ``deep``   n x 96 L2-normalised: ``components`` components (128 by
+  default), means N(0,1)^96, sigma 0.3, then normalised; inner-product search;
+  graph built with L2 on the unit vectors (equivalent ordering to -IP).
+
+The entry point is the base point nearest (FP64 L2) to the mean of the base
+set, ties to the smaller id (a cheap stand-in for the medoid).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _cache_dir() -> str:
+    return os.environ.get("ANN_SYNTH_CACHE", os.path.join(_REPO, ".synth_cache"))
+
+
+@dataclass
+class Workload:
+    name: str
+    base: np.ndarray          # n x d float32
+    queries: np.ndarray       # nq x d float32
+    adj: np.ndarray           # n x R int32, -1 padded
+    entry: int
+    metric: str               # "l2" or "ip"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return self.base.shape[0]
+
+    @property
+    def d(self):
+        return self.base.shape[1]
+
+    @property
+    def R(self):
+        return self.adj.shape[1]
+
+
+# --------------------------------------------------------------- point sets
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _labels(rng, count, C):
+    return rng.integers(0, C, size=count)
+
+
+def mixture_tiny(n, nq, d=32, C=16, sigma=0.15, seed=100):
+    means = _rng(seed + 7).uniform(-1.0, 1.0, size=(C, d))
+    def draw(count, s):
+        r = _rng(s)
+        lab = _labels(r, count, C)
+        return (means[lab] + sigma * r.standard_normal((count, d))).astype(np.float32)
+    return draw(n, seed + 1), draw(nq, seed + 2)
+
+
+def mixture_sift(n, nq, d=128, C=64, sigma=30.0, seed=200):
+    means = _rng(seed + 7).uniform(0.0, 255.0, size=(C, d)) * 0.6 + 51.0
+    def draw(count, s):
+        r = _rng(s)
+        lab = _labels(r, count, C)
+        out = np.empty((count, d), np.float32)
+        step = 1 << 16
+        for a in range(0, count, step):
+            b = min(count, a + step)
+            v = means[lab[a:b]] + sigma * r.standard_normal((b - a, d))
+            out[a:b] = np.clip(np.rint(v), 0.0, 255.0)
+        return out
+    return draw(n, seed + 1), draw(nq, seed + 2)
+
+
+def mixture_gist(n, nq, d=960, C=32, seed=300):
+    mus = _rng(seed + 7).normal(-2.0, 0.5, size=(C, d))
+    def draw(count, s):
+        r = _rng(s)
+        lab = _labels(r, count, C)
+        out = np.empty((count, d), np.float32)
+        step = 1 << 14
+        for a in range(0, count, step):
+            b = min(count, a + step)
+            out[a:b] = np.exp(mus[lab[a:b]] + 0.5 * r.standard_normal((b - a, d)))
+        return out
+    return draw(n, seed + 1), draw(nq, seed + 2)
+
+
+def mixture_deep(n, nq, d=96, C=128, sigma=0.3, seed=400):
+    means = _rng(seed + 7).standard_normal((C, d))
+    def draw(count, s):
+        r = _rng(s)
+        lab = _labels(r, count, C)
+        out = np.empty((count, d), np.float32)
+        step = 1 << 16
+        for a in range(0, count, step):
+            b = min(count, a + step)
+            v = means[lab[a:b]] + sigma * r.standard_normal((b - a, d))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            out[a:b] = v
+        return out
+    return draw(n, seed + 1), draw(nq, seed + 2)
+
+
+# ------------------------------------------------------------ graph builder
+
+def _torch_device():
+    import torch
+    return torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+
+
+def knn_lists(x: np.ndarray, k: int, exact64: bool = False, chunk_elems: int = 1 << 31):
+    """k nearest other points of every point by L2 (self excluded), sorted by
+    ascending distance. Returns (ids int32 n x k, squared distances float32).
+    Chunked ||a||^2 + ||b||^2 - 2 a.b on whatever torch device is present;
+    ``exact64`` computes in float64 (small sets)."""
+    import torch
+    dev = torch.device("cpu") if exact64 else _torch_device()
+    dt = torch.float64 if exact64 else torch.float32
+    n = x.shape[0]
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        X = torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)
+        nrm = (X * X).sum(1)
+        ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+        dst = torch.empty((n, k), dtype=torch.float32, device=dev)
+        step = max(1, min(8192, chunk_elems // max(n, 1)))
+        for a in range(0, n, step):
+            b = min(n, a + step)
+            D = nrm[a:b, None] + nrm[None, :] - 2.0 * (X[a:b] @ X.T)
+            D.clamp_(min=0)
+            D[torch.arange(b - a, device=dev), torch.arange(a, b, device=dev)] = float("inf")
+            v, i = torch.topk(D, k, dim=1, largest=False, sorted=True)
+            ids[a:b] = i.to(torch.int32)
+            dst[a:b] = v.to(torch.float32)
+            del D
+        return ids.cpu().numpy(), dst.cpu().numpy()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def occlusion_prune(x: np.ndarray, cand: np.ndarray, cand_d: np.ndarray, R: int, batch: int = 16384):
+    """NSG-style occlusion rule over each point's sorted candidate list: keep
+    candidate c_j unless an already kept c_i is closer to c_j than the point
+    itself is; stop at R kept. Returns int32 n x R, -1 padded."""
+    import torch
+    dev = _torch_device()
+    n, k = cand.shape
+    X = torch.from_numpy(np.ascontiguousarray(x)).to(dev, torch.float32)
+    out = np.full((n, R), -1, np.int32)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for a in range(0, n, batch):
+            b = min(n, a + batch)
+            C = torch.from_numpy(cand[a:b].astype(np.int64)).to(dev)
+            dpc = torch.from_numpy(cand_d[a:b]).to(dev)
+            V = X[C]                                     # B x k x d
+            nv = (V * V).sum(-1)                         # B x k
+            D = nv[:, :, None] + nv[:, None, :] - 2.0 * torch.bmm(V, V.transpose(1, 2))
+            kept = torch.zeros((b - a, k), dtype=torch.bool, device=dev)
+            cnt = torch.zeros(b - a, dtype=torch.int32, device=dev)
+            for j in range(k):
+                occl = (kept & (D[:, :, j] < dpc[:, j:j + 1])).any(1)
+                keep = (~occl) & (cnt < R)
+                kept[:, j] = keep
+                cnt += keep.to(torch.int32)
+            # gather kept ids in order
+            order = torch.where(kept, torch.arange(k, device=dev)[None, :].expand(b - a, k),
+                                torch.full_like(C, k))
+            order, _ = torch.sort(order, dim=1)
+            order = order[:, :R]
+            valid = order < k
+            sel = torch.gather(C, 1, order.clamp(max=k - 1))
+            sel = torch.where(valid, sel, torch.full_like(sel, -1))
+            w = sel.shape[1]
+            out[a:b, :w] = sel.cpu().numpy().astype(np.int32)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
+def _edge_dist(x, src, dst):
+    out = np.empty(src.shape[0], np.float64)
+    step = 1 << 20
+    for a in range(0, src.shape[0], step):
+        b = min(src.shape[0], a + step)
+        diff = x[src[a:b]].astype(np.float64) - x[dst[a:b]].astype(np.float64)
+        out[a:b] = np.einsum("ij,ij->i", diff, diff)
+    return out
+
+
+def reverse_fill(x: np.ndarray, fwd: np.ndarray, R: int) -> np.ndarray:
+    """Widen a -1 padded forward list to R columns and fill free slots of
+    each vertex c with reverse edges c -> p (for forward edges p -> c), by
+    ascending distance, skipping ones already present."""
+    n = fwd.shape[0]
+    adj = np.full((n, R), -1, np.int32)
+    w = min(R, fwd.shape[1])
+    adj[:, :w] = fwd[:, :w]
+    deg = (adj >= 0).sum(1).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), R)
+    dst = adj.reshape(-1).astype(np.int64)
+    m = dst >= 0
+    src, dst = src[m], dst[m]
+    fwd_keys = src * n + dst
+    # candidate reverse edge: owner = dst, target = src
+    owner, target = dst, src
+    rev_keys = owner * n + target
+    keep = ~np.isin(rev_keys, fwd_keys)
+    owner, target = owner[keep], target[keep]
+    dist = _edge_dist(x, owner, target)
+    order = np.lexsort((target, dist, owner))
+    owner, target = owner[order], target[order]
+    first = np.searchsorted(owner, owner, side="left")
+    rank = np.arange(owner.shape[0]) - first
+    free = R - deg[owner]
+    take = rank < free
+    owner, target, rank = owner[take], target[take], rank[take]
+    adj[owner, deg[owner] + rank] = target.astype(np.int32)
+    return adj
+
+
+def entry_point(x: np.ndarray) -> int:
+    """Base point nearest (FP64 L2) to the mean of the base set; ties to the
+    smaller id."""
+    mean = x.astype(np.float64).mean(0)
+    best, best_i = np.inf, 0
+    step = 1 << 16
+    for a in range(0, x.shape[0], step):
+        b = min(x.shape[0], a + step)
+        diff = x[a:b].astype(np.float64) - mean
+        dd = np.einsum("ij,ij->i", diff, diff)
+        i = int(np.argmin(dd))
+        if dd[i] < best:
+            best, best_i = float(dd[i]), a + i
+    return best_i
+
+
+def reachable_from(adj: np.ndarray, entry: int) -> np.ndarray:
+    """Boolean mask of vertices reachable from ``entry`` along directed edges."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    n, R = adj.shape
+    rows = np.repeat(np.arange(n), R)
+    cols = adj.reshape(-1)
+    m = cols >= 0
+    g = sp.csr_matrix((np.ones(int(m.sum()), np.int8), (rows[m], cols[m])), shape=(n, n))
+    order = breadth_first_order(g, entry, directed=True, return_predecessors=False)
+    mask = np.zeros(n, bool)
+    mask[order] = True
+    return mask
+
+
+def repair_reachability(adj: np.ndarray, entry: int, knn: np.ndarray, x: np.ndarray,
+                        max_rounds: int = 4096):
+    """Make every vertex reachable from ``entry``. Each round links the
+    unreachable vertices that have a reachable k-NN neighbour from the nearest
+    such neighbour; if none has one, the unreachable vertex nearest to the
+    reachable set (FP64 L2, brute force) is linked from its nearest reachable
+    vertex. A link takes a free slot if there is one, else the last slot not
+    already holding a link added here. Returns (adj, number of links added)."""
+    adj = adj.copy()
+    n, R = adj.shape
+    protected = np.zeros((n, R), bool)
+    added = 0
+
+    def link(src, u):
+        nonlocal added
+        row = adj[src]
+        if u in row:
+            return
+        free = np.flatnonzero(row < 0)
+        if free.size:
+            slot = int(free[0])
+        else:
+            cand = np.flatnonzero(~protected[src])
+            if cand.size == 0:
+                return
+            slot = int(cand[-1])
+        row[slot] = u
+        protected[src, slot] = True
+        added += 1
+
+    for _ in range(max_rounds):
+        mask = reachable_from(adj, entry)
+        un = np.flatnonzero(~mask)
+        if un.size == 0:
+            return adj, added
+        progressed = False
+        for u in un:
+            for v in knn[u]:
+                if v >= 0 and mask[v]:
+                    link(int(v), int(u))
+                    progressed = True
+                    break
+        if not progressed:
+            reach = np.flatnonzero(mask)
+            xr = x[reach].astype(np.float64)
+            best = (np.inf, -1, -1)
+            for u in un[: min(un.size, 256)]:
+                diff = xr - x[u].astype(np.float64)
+                dd = np.einsum("ij,ij->i", diff, diff)
+                i = int(np.argmin(dd))
+                if dd[i] < best[0]:
+                    best = (float(dd[i]), int(reach[i]), int(u))
+            link(best[1], best[2])
+    raise RuntimeError("graph repair did not converge")
+
+
+# ---------------------------------------------------------------- builders
+
+def build_knn_reverse_graph(x, k=16, cap=24):
+    """Exact k-NN (FP64, L2, self excluded) then reverse edges to ``cap``."""
+    ids, _ = knn_lists(x, k, exact64=True)
+    return reverse_fill(x, ids, cap), ids
+
+
+def build_pruned_graph(x, R=32, k=64):
+    """k-NN candidates, occlusion prune to R, reverse fill to R."""
+    ids, dd = knn_lists(x, k)
+    pruned = occlusion_prune(x, ids, dd, R)
+    return reverse_fill(x, pruned, R), ids
+
+
+def _key(d):
+    return hashlib.sha1(json.dumps(d, sort_keys=True).encode()).hexdigest()[:16]
+
+
+def _load_or_build(spec: dict, fn):
+    cdir = _cache_dir()
+    path = os.path.join(cdir, spec["kind"] + "_" + _key(spec) + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return {k: z[k] for k in z.files}
+    out = fn()
+    os.makedirs(cdir, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, **out)
+    os.replace(tmp, path)
+    return out
+
+
+def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | None = None,
+                  components: int | None = None, cache: bool = True) -> Workload:
+    """Build (or load from the cache) a seeded workload of the given shape."""
+    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 1}
+
+    def gen():
+        if kind == "tiny":
+            base, q = mixture_tiny(n, nq, d=d or 32, C=components or 16)
+            adj, knn = build_knn_reverse_graph(base, k=16, cap=R or 24)
+        elif kind == "sift":
+            base, q = mixture_sift(n, nq, d=d or 128, C=components or 64)
+            adj, knn = build_pruned_graph(base, R=R or 32)
+        elif kind == "gist":
+            base, q = mixture_gist(n, nq, d=d or 960, C=components or 32)
+            adj, knn = build_pruned_graph(base, R=R or 32)
+        elif kind == "deep":
+            base, q = mixture_deep(n, nq, d=d or 96, C=components or 128)
+            adj, knn = build_pruned_graph(base, R=R or 32)
+        else:
+            raise ValueError(kind)
+        entry = entry_point(base)
+        adj, added = repair_reachability(adj, entry, knn, base)
+        return {"base": base, "queries": q, "adj": adj, "entry": np.array(entry),
+                "repaired": np.array(added)}
+
+    z = _load_or_build(spec, gen) if cache else gen()
+    metric = "ip" if kind == "deep" else "l2"
+    return Workload(name=kind, base=z["base"], queries=z["queries"], adj=z["adj"],
+                    entry=int(z["entry"]), metric=metric,
+                    meta={"repaired_links": int(z["repaired"]), **spec})
+
+
+def random_graph(n, d, R, seed, metric="l2", nq=8, pad_frac=0.0, dup_frac=0.0):
+    """Small adversarial inputs for tests: uniform random points, R random
+    out-edges per vertex (with optional -1 padding and duplicated vectors)."""
+    r = _rng(seed)
+    base = r.standard_normal((n, d)).astype(np.float32)
+    if dup_frac > 0:
+        k = int(n * dup_frac)
+        src = r.integers(0, n, size=k)
+        dst = r.integers(0, n, size=k)
+        base[dst] = base[src]
+    adj = np.empty((n, R), np.int32)
+    for i in range(n):
+        adj[i] = r.choice(np.delete(np.arange(n), i), size=R, replace=R > n - 1)
+    if pad_frac > 0:
+        adj[r.random((n, R)) < pad_frac] = -1
+    if metric == "ip":
+        base /= np.linalg.norm(base, axis=1, keepdims=True)
+    q = r.standard_normal((nq, d)).astype(np.float32)
+    if metric == "ip":
+        q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return base, adj, q
