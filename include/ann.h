@@ -164,56 +164,6 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
 /* Message of the last failing call on this thread ("" if none). */
 const char *ann_last_error(void);
 
-/* ---------------------------------------------------------------- serving
- * Continuous batching: requests are submitted one at a time from the host
- * and admitted to the GPU as request slots and device scratch free up; the
- * library's scheduler thread groups the admitted requests into launches on
- * several streams so work that arrives while other work is running overlaps
- * with it on the device. Each request's result is the same as a single
- * ann_search of that query with the same k, L, M (sync mode). */
-
-typedef struct {
-    int32_t slots;          /* requests admitted at once (device-resident state); 0 = 4096 */
-    int32_t max_batch;      /* queries per launch; 0 = 1024 */
-    int32_t streams;        /* launches in flight; 0 = 4 */
-    int32_t max_k;          /* per-request limits; 0 = 100 / 1024 / 32 */
-    int32_t max_L;
-    int32_t max_M;
-    int32_t mode;           /* ann_mode for every request */
-    int32_t rerank;         /* as in ann_search_params */
-    int64_t scratch_bytes;  /* device bytes for request state; 0 = derived from slots */
-} ann_serve_config;
-
-typedef struct ann_server ann_server;
-
-typedef struct {
-    uint64_t tag;           /* the caller's tag from ann_serve_submit */
-    int32_t k;              /* valid entries in ids / dists */
-    int32_t status;         /* ANN_OK or the request's error */
-    double latency_us;      /* submit to completion, host clock */
-    double device_us;       /* the query's own time on the device */
-} ann_result;
-
-/* Create a server over an index (the index must outlive it). */
-int ann_serve_create(const ann_index *index, const ann_serve_config *cfg, ann_server **out);
-
-/* Drain in-flight work, stop the scheduler and free everything. NULL is a no-op. */
-void ann_serve_destroy(ann_server *server);
-
-/* Submit one query (host pointer, d float32; copied before return) with its
- * own k, L, M. Returns ANN_ERR_BUSY without blocking when every slot is
- * taken, ANN_ERR_ARG for limits outside the config. */
-int ann_serve_submit(ann_server *server, const float *query, int32_t k, int32_t L, int32_t M,
-                     uint64_t tag);
-
-/* Collect up to max completed requests. results[i] describes request i;
- * its ids / dists are written to out_ids + i * cfg.max_k and
- * out_dists + i * cfg.max_k (host). Waits at most timeout_us microseconds
- * for the first completion; returns the number collected (>= 0), or
- * ANN_ERR_TIMEOUT when nothing completed in time. */
-int ann_serve_poll(ann_server *server, ann_result *results, int64_t *out_ids, float *out_dists,
-                   int32_t max, int32_t timeout_us);
-
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,119 @@
+"""ctypes declarations of the C ABI in include/ann.h (libann.so).
+
+Names match the C entry points. Every function raises ``AnnError`` with the
+library's message when the C call returns a non-zero status. There is no
+fallback: if libann.so is missing the first call fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+ANN_OK = 0
+ANN_ERR_ARG, ANN_ERR_OOM, ANN_ERR_CUDA, ANN_ERR_BUSY, ANN_ERR_TIMEOUT, ANN_ERR_STATE = -1, -2, -3, -4, -5, -6
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3}
+METRIC = {"l2": 0, "ip": 1}
+MODE = {"sync": 0, "async": 1}
+ANN_INDEX_DEVICE_INPUT = 0x1
+ANN_INDEX_KEEP_F32 = 0x2
+
+
+class AnnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libann error {code}: {msg}")
+        self.code = code
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("d_pad", ctypes.c_int32),
+                ("R", ctypes.c_int32), ("storage", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("has_f32", ctypes.c_int32), ("entry", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("expansions", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("hash_resets", ctypes.c_int64), ("dup_dropped", ctypes.c_int64),
+                ("merges", ctypes.c_int64), ("t_start_ns", ctypes.c_int64), ("t_end_ns", ctypes.c_int64)]
+
+
+STATS_FIELDS = [f for f, _ in QueryStats._fields_]
+
+
+class SearchParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("M0", ctypes.c_int32), ("t", ctypes.c_int32),
+                ("R_ratio", ctypes.c_float), ("rerank", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("hash_bits", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
+                ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libann.so (compiling it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build.needs_build():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise AnnError(ANN_ERR_STATE, f"{path} is missing; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.ann_index_create.argtypes = [vp, i64, i32, i32, vp, i32, i64, i32, i32, ctypes.POINTER(vp)]
+            L.ann_index_destroy.argtypes = [vp]
+            L.ann_index_destroy.restype = None
+            L.ann_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+            L.ann_search.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
+            L.ann_search_ex.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
+            L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
+            L.ann_last_error.restype = ctypes.c_char_p
+            L.ann_last_error.argtypes = []
+            _lib = L
+    return _lib
+
+
+def ann_last_error() -> str:
+    return lib().ann_last_error().decode(errors="replace")
+
+
+def _check(rc):
+    if rc != ANN_OK:
+        raise AnnError(rc, ann_last_error())
+
+
+def ann_index_create(base, n, d, storage, adj, R, entry, metric, flags) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().ann_index_create(base, n, d, storage, adj, R, entry, metric, flags, ctypes.byref(out)))
+    return out.value
+
+
+def ann_index_destroy(index) -> None:
+    lib().ann_index_destroy(index)
+
+
+def ann_index_get_info(index) -> IndexInfo:
+    info = IndexInfo()
+    _check(lib().ann_index_get_info(index, ctypes.byref(info)))
+    return info
+
+
+def ann_search(index, queries, nq, k, L, M, out_ids, out_dists, stream) -> None:
+    _check(lib().ann_search(index, queries, nq, k, L, M, out_ids, out_dists, stream))
+
+
+def ann_search_ex(index, queries, nq, k, L, M, out_ids, out_dists, params, stream) -> None:
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().ann_search_ex(index, queries, nq, k, L, M, out_ids, out_dists, p, stream))
+
+
+def ann_search_host(index, queries, nq, k, L, M, out_ids, out_dists, params, stream) -> None:
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().ann_search_host(index, queries, nq, k, L, M, out_ids, out_dists, p, stream))

@@ -1,0 +1,344 @@
+// ann_api.cu -- host side of the C ABI declared in include/ann.h: argument
+// checks, index memory, kernel selection and launch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "ann_internal.cuh"
+
+struct ann_index {
+    ann::IndexData d;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ANN_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(ANN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ANN_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+void free_index_data(ann::IndexData &x) {
+    cudaFree(x.base);
+    cudaFree(x.scales);
+    if (x.owns_base32) cudaFree(x.base32);
+    cudaFree(x.adj);
+    cudaFree(x.stage);
+    cudaFree(x.work_counter);
+    x = ann::IndexData();
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int max_dyn_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+int create_impl(const float *base, int64_t n, int32_t d, int32_t storage, const int32_t *adj, int32_t R,
+                int64_t entry, int32_t metric, int32_t flags, ann_index **out) {
+    if (!out) return fail(ANN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!base || !adj) return fail(ANN_ERR_ARG, "base and adj must not be NULL");
+    if (n < 1 || n >= (1ll << 31) - 1) return fail(ANN_ERR_ARG, "n=%lld outside [1, 2^31-1)", (long long)n);
+    if (d < 1 || d > 4096) return fail(ANN_ERR_ARG, "d=%d outside [1, 4096]", d);
+    if (R < 1 || R > 256) return fail(ANN_ERR_ARG, "R=%d outside [1, 256]", R);
+    if (entry < 0 || entry >= n) return fail(ANN_ERR_ARG, "entry=%lld outside [0, n)", (long long)entry);
+    if (storage < ANN_STORE_F32 || storage > ANN_STORE_E4M3) return fail(ANN_ERR_ARG, "unknown storage %d", storage);
+    if (metric != ANN_METRIC_L2 && metric != ANN_METRIC_IP) return fail(ANN_ERR_ARG, "unknown metric %d", metric);
+    if (flags & ~(ANN_INDEX_DEVICE_INPUT | ANN_INDEX_KEEP_F32)) return fail(ANN_ERR_ARG, "unknown flags 0x%x", flags);
+    const bool dev_in = flags & ANN_INDEX_DEVICE_INPUT;
+    if (!dev_in) {
+        for (int64_t i = 0; i < n * (int64_t)R; ++i)
+            if (adj[i] < -1 || (int64_t)adj[i] >= n)
+                return fail(ANN_ERR_ARG, "adj[%lld]=%d outside [-1, n)", (long long)i, adj[i]);
+    }
+
+    ann::IndexData x;
+    cudaGetDevice(&x.device);
+    x.n = n;
+    x.d = d;
+    x.R = R;
+    x.storage = storage;
+    x.metric = metric;
+    x.entry = entry;
+    const int es = ann::storage_bytes(storage);
+    const int per16 = 16 / es;
+    x.d_pad = (d + per16 - 1) / per16 * per16;
+    x.d_pad32 = (d + 3) / 4 * 4;
+
+    auto cleanup_fail = [&](int code) {
+        free_index_data(x);
+        return code;
+    };
+    cudaError_t e;
+    const size_t base_bytes = (size_t)n * x.d_pad * es;
+    if ((e = cudaMalloc(&x.base, base_bytes)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(base)"));
+    if ((e = cudaMalloc(&x.adj, (size_t)n * R * 4)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(adj)"));
+    if ((e = cudaMalloc(&x.work_counter, 64)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(counter)"));
+    x.device_bytes = base_bytes + (size_t)n * R * 4;
+    if (storage == ANN_STORE_E4M3) {
+        if ((e = cudaMalloc(&x.scales, (size_t)n * 4)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(scales)"));
+        x.device_bytes += (size_t)n * 4;
+    }
+    const bool keep32 = storage != ANN_STORE_F32 && (flags & ANN_INDEX_KEEP_F32);
+    if (keep32) {
+        if ((e = cudaMalloc(&x.base32, (size_t)n * x.d_pad32 * 4)) != cudaSuccess)
+            return cleanup_fail(cuda_fail(e, "cudaMalloc(base32)"));
+        x.owns_base32 = true;
+        x.device_bytes += (size_t)n * x.d_pad32 * 4;
+    } else if (storage == ANN_STORE_F32) {
+        x.base32 = reinterpret_cast<float *>(x.base);
+    }
+
+    // stage FP32 input on the device if it is on the host
+    const float *src = base;
+    float *tmp = nullptr;
+    if (!dev_in) {
+        if ((e = cudaMalloc(&tmp, (size_t)n * d * 4)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(tmp)"));
+        if ((e = cudaMemcpy(tmp, base, (size_t)n * d * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            cudaFree(tmp);
+            return cleanup_fail(cuda_fail(e, "cudaMemcpy(base)"));
+        }
+        src = tmp;
+        if ((e = cudaMemcpy(x.adj, adj, (size_t)n * R * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            cudaFree(tmp);
+            return cleanup_fail(cuda_fail(e, "cudaMemcpy(adj)"));
+        }
+    } else {
+        if ((e = cudaMemcpy(x.adj, adj, (size_t)n * R * 4, cudaMemcpyDeviceToDevice)) != cudaSuccess)
+            return cleanup_fail(cuda_fail(e, "cudaMemcpy(adj)"));
+        unsigned long long *bad = nullptr;
+        if ((e = cudaMalloc(&bad, 8)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(bad)"));
+        unsigned long long hbad = 0;
+        e = cudaMemset(bad, 0, 8);
+        if (e == cudaSuccess) e = ann::launch_count_bad_adj(x.adj, n * (int64_t)R, n, bad, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, 8, cudaMemcpyDeviceToHost);
+        cudaFree(bad);
+        if (e != cudaSuccess) return cleanup_fail(cuda_fail(e, "adjacency check"));
+        if (hbad) return cleanup_fail(fail(ANN_ERR_ARG, "%llu adjacency ids outside [-1, n)", hbad));
+    }
+    e = ann::launch_encode(src, n, d, storage, x.base, x.d_pad, x.scales, 0);
+    if (e == cudaSuccess && keep32) e = ann::launch_encode(src, n, d, ANN_STORE_F32, x.base32, x.d_pad32, nullptr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cleanup_fail(cuda_fail(e, "encode"));
+
+    ann_index *ix = new (std::nothrow) ann_index;
+    if (!ix) return cleanup_fail(fail(ANN_ERR_OOM, "host allocation"));
+    ix->d = x;
+    *out = ix;
+    return ANN_OK;
+}
+
+struct Plan {
+    ann::SearchArgs a;
+    int threads;
+    int smem;
+    int grid;
+};
+
+int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
+                int64_t *out_ids, float *out_dists, const ann_search_params *p, Plan *plan) {
+    if (!index) return fail(ANN_ERR_ARG, "index is NULL");
+    const ann::IndexData &x = index->d;
+    if (nq < 0) return fail(ANN_ERR_ARG, "nq=%lld < 0", (long long)nq);
+    if (nq > 0 && (!queries || !out_ids || !out_dists)) return fail(ANN_ERR_ARG, "queries/out pointers must not be NULL");
+    if (L < 1 || L > 2048) return fail(ANN_ERR_ARG, "L=%d outside [1, 2048]", L);
+    if (k < 1 || k > L) return fail(ANN_ERR_ARG, "k=%d outside [1, L=%d]", k, L);
+    if (M < 1 || M > 64) return fail(ANN_ERR_ARG, "M=%d outside [1, 64]", M);
+    ann_search_params def;
+    memset(&def, 0, sizeof(def));
+    if (!p) p = &def;
+    if (p->mode != ANN_MODE_SYNC) return fail(ANN_ERR_ARG, "mode %d is not available in this build", p->mode);
+    const int M0 = p->M0 ? p->M0 : 1;
+    const int t = p->t ? p->t : 1;
+    if (M0 < 1 || t < 1) return fail(ANN_ERR_ARG, "M0=%d and t=%d must be >= 1", M0, t);
+    if (p->rerank && !x.base32) return fail(ANN_ERR_ARG, "rerank needs an FP32 copy (ANN_INDEX_KEEP_F32)");
+    int threads = p->threads;
+    if (threads == 0) threads = (M * x.R >= 256) ? 256 : 128;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
+    int hb = p->hash_bits;
+    if (hb == 0) hb = L > 512 ? 14 : 13;
+    if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
+
+    ann::SearchArgs &a = plan->a;
+    memset(&a, 0, sizeof(a));
+    a.base = x.base;
+    a.scales = x.scales;
+    a.base32 = x.base32;
+    a.adj = x.adj;
+    a.n = x.n;
+    a.d = x.d;
+    a.d_pad = x.d_pad;
+    a.d_pad32 = x.d_pad32;
+    a.R = x.R;
+    a.entry = x.entry;
+    a.metric = x.metric;
+    a.queries = queries;
+    a.nq = nq;
+    a.k = k;
+    a.L = L;
+    a.M = M;
+    a.k_arr = p->k_per_query;
+    a.L_arr = p->L_per_query;
+    a.M_arr = p->M_per_query;
+    a.M0 = M0;
+    a.t = t;
+    a.R_ratio = p->R_ratio;
+    a.rerank = p->rerank ? 1 : 0;
+    a.hash_bits = hb;
+    a.out_ids = out_ids;
+    a.out_dists = out_dists;
+    a.stats = p->stats;
+    a.work_counter = x.work_counter;
+    a.persistent = p->persistent ? 1 : 0;
+    a.Lcap = L;
+    int need = M * x.R;
+    if (a.rerank && L > need) need = L;
+    a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
+    a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
+    ann::SmemLayout lay = ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M);
+    if (lay.total > max_dyn_smem())
+        return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
+                    lay.total, max_dyn_smem());
+    plan->threads = threads;
+    plan->smem = lay.total;
+    plan->grid = (int)(nq > 0x7fffffff ? 0x7fffffff : nq);
+    if (a.persistent && nq > 0) {
+        int bps = 0;
+        cudaError_t e = ann::sync_search_occupancy(x.storage, threads, lay.total, &bps);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+        if (bps < 1) return fail(ANN_ERR_ARG, "kernel does not fit on an SM");
+        int64_t g = (int64_t)bps * sm_count();
+        plan->grid = (int)(g < nq ? g : nq);
+    }
+    return ANN_OK;
+}
+
+int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
+    if (plan.a.nq == 0) return ANN_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != index->d.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, index->d.device);
+    if (plan.a.persistent) ANN_CUDA(cudaMemsetAsync(index->d.work_counter, 0, sizeof(int), s));
+    cudaError_t e = ann::launch_sync_search(plan.a, index->d.storage, plan.threads, plan.smem, plan.grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "search launch");
+    return ANN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ann_index_create(const float *base, int64_t n, int32_t d, int32_t storage, const int32_t *adj, int32_t R,
+                     int64_t entry, int32_t metric, int32_t flags, ann_index **out) {
+    return create_impl(base, n, d, storage, adj, R, entry, metric, flags, out);
+}
+
+void ann_index_destroy(ann_index *index) {
+    if (!index) return;
+    free_index_data(index->d);
+    delete index;
+}
+
+int ann_index_get_info(const ann_index *index, ann_index_info *info) {
+    if (!index || !info) return fail(ANN_ERR_ARG, "index and info must not be NULL");
+    const ann::IndexData &x = index->d;
+    info->n = x.n;
+    info->d = x.d;
+    info->d_pad = x.d_pad;
+    info->R = x.R;
+    info->storage = x.storage;
+    info->metric = x.metric;
+    info->has_f32 = x.base32 != nullptr;
+    info->entry = x.entry;
+    info->device_bytes = x.device_bytes;
+    return ANN_OK;
+}
+
+int ann_search_ex(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
+                  int64_t *out_ids, float *out_dists, const ann_search_params *params, void *stream) {
+    Plan plan;
+    int rc = plan_search(index, queries, nq, k, L, M, out_ids, out_dists, params, &plan);
+    if (rc != ANN_OK) return rc;
+    return launch_plan(index, plan, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ann_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
+               int64_t *out_ids, float *out_dists, void *stream) {
+    return ann_search_ex(index, queries, nq, k, L, M, out_ids, out_dists, nullptr, stream);
+}
+
+int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
+                    int64_t *out_ids, float *out_dists, const ann_search_params *params, void *stream) {
+    if (!index) return fail(ANN_ERR_ARG, "index is NULL");
+    if (nq == 0) return ANN_OK;
+    ann::IndexData &x = index->d;
+    const size_t qb = (size_t)nq * x.d * 4, ib = (size_t)nq * k * 8, db = (size_t)nq * k * 4;
+    const size_t need = ((qb + 255) & ~size_t(255)) + ((ib + 255) & ~size_t(255)) + db;
+    // validate before touching the staging buffers (device pointers are placeholders here)
+    Plan plan;
+    int rc = plan_search(index, reinterpret_cast<const float *>(16), nq, k, L, M,
+                         reinterpret_cast<int64_t *>(16), reinterpret_cast<float *>(16), params, &plan);
+    if (rc != ANN_OK) return rc;
+    if (!queries || !out_ids || !out_dists) return fail(ANN_ERR_ARG, "host pointers must not be NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (x.stage_bytes < need) {
+        ANN_CUDA(cudaStreamSynchronize(s));
+        cudaFree(x.stage);
+        x.stage = nullptr;
+        x.stage_bytes = 0;
+        ANN_CUDA(cudaMalloc(&x.stage, need));
+        x.stage_bytes = need;
+    }
+    char *st = reinterpret_cast<char *>(x.stage);
+    float *dq = reinterpret_cast<float *>(st);
+    int64_t *dids = reinterpret_cast<int64_t *>(st + ((qb + 255) & ~size_t(255)));
+    float *ddist = reinterpret_cast<float *>(st + ((qb + 255) & ~size_t(255)) + ((ib + 255) & ~size_t(255)));
+    plan.a.queries = dq;
+    plan.a.out_ids = dids;
+    plan.a.out_dists = ddist;
+    ANN_CUDA(cudaMemcpyAsync(dq, queries, qb, cudaMemcpyHostToDevice, s));
+    rc = launch_plan(index, plan, s);
+    if (rc != ANN_OK) return rc;
+    ANN_CUDA(cudaMemcpyAsync(out_ids, dids, ib, cudaMemcpyDeviceToHost, s));
+    ANN_CUDA(cudaMemcpyAsync(out_dists, ddist, db, cudaMemcpyDeviceToHost, s));
+    ANN_CUDA(cudaStreamSynchronize(s));
+    return ANN_OK;
+}
+
+const char *ann_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// ann_internal.cuh -- shared declarations of libann's host code and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ann.h"
+
+namespace ann {
+
+// Packed queue / candidate entry: (order-preserving key bits << 32) | id,
+// with bit 31 of the id word holding the "checked" flag of Algorithm 1. Two
+// entries compare in (key, id) order once the flag is masked off.
+typedef unsigned long long entry_t;
+static constexpr entry_t kChecked = 1ull << 31;
+static constexpr entry_t kMask = ~kChecked;
+static constexpr entry_t kEmptyEntry = ~0ull;
+static constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
+
+struct IndexData {
+    int device = 0;
+    int64_t n = 0;
+    int32_t d = 0, d_pad = 0, R = 0;
+    int32_t storage = ANN_STORE_F32, metric = ANN_METRIC_L2;
+    int64_t entry = 0;
+    void *base = nullptr;       // n x d_pad, storage type, zero padded
+    float *scales = nullptr;    // n, E4M3 only
+    float *base32 = nullptr;    // n x d_pad32 FP32 rows for re-rank (aliases base for F32)
+    int32_t d_pad32 = 0;
+    int32_t *adj = nullptr;     // n x R
+    bool owns_base32 = false;
+    int64_t device_bytes = 0;
+    // staging for ann_search_host
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // device counter for the persistent grid
+    int *work_counter = nullptr;
+};
+
+// Everything a search launch needs, passed by value.
+struct SearchArgs {
+    const void *base;
+    const float *scales;
+    const float *base32;
+    const int32_t *adj;
+    int64_t n;
+    int32_t d, d_pad, d_pad32, R;
+    int64_t entry;
+    int32_t metric;
+    const float *queries;
+    int64_t nq;
+    int32_t k, L, M;  // maxima (uniform values when no per-query arrays)
+    const int32_t *k_arr, *L_arr, *M_arr;
+    int32_t M0, t;
+    float R_ratio;
+    int32_t rerank;
+    int32_t hash_bits;
+    int64_t *out_ids;
+    float *out_dists;
+    ann_query_stats *stats;
+    int *work_counter;
+    int32_t persistent;
+    // shared-memory layout
+    int32_t Lcap;        // queue capacity
+    int32_t Ccap;        // candidate / sort buffer, power of two >= 32
+    int32_t qfloats;     // query buffer length
+};
+
+// Byte offsets of the dynamic shared-memory segments (16-byte aligned).
+struct SmemLayout {
+    int q_off, q0_off, q1_off, cand_off, dup_off, hash_off, act_off, total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap) {
+    SmemLayout s;
+    int o = 0;
+    s.q_off = o;    o += align16(qfloats * 4);
+    s.q0_off = o;   o += align16(Lcap * 8);
+    s.q1_off = o;   o += align16(Lcap * 8);
+    s.cand_off = o; o += align16(Ccap * 8);
+    s.dup_off = o;  o += align16(Ccap);
+    s.hash_off = o; o += align16((1 << hash_bits) * 4);
+    s.act_off = o;  o += align16(Mcap * 4);
+    s.total = o;
+    return s;
+}
+
+inline int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+inline int storage_bytes(int storage) {
+    switch (storage) {
+        case ANN_STORE_F32: return 4;
+        case ANN_STORE_BF16: return 2;
+        case ANN_STORE_F16: return 2;
+        case ANN_STORE_E4M3: return 1;
+    }
+    return 0;
+}
+
+// kernels/launchers (search_sync.cu)
+cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, int smem_bytes,
+                               int grid, cudaStream_t stream);
+cudaError_t sync_search_occupancy(int storage, int threads, int smem_bytes, int *blocks_per_sm);
+
+// encode.cu
+cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, void *dst, int32_t d_pad,
+                          float *scales, cudaStream_t stream);
+cudaError_t launch_count_bad_adj(const int32_t *adj, int64_t count, int64_t n, unsigned long long *bad,
+                                 cudaStream_t stream);
+
+}  // namespace ann

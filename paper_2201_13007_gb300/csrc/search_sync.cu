@@ -1,0 +1,324 @@
+// search_sync.cu -- bulk-synchronous top-M best-first search, one CTA per query.
+//
+// Follows Algorithm 1 (BFiS) generalised by Sec. 4.1 to expand the top-M
+// unchecked candidates per step, with the Sec. 4.2 staged schedule (M starts
+// at M0 and doubles every t steps up to M_max). Every step is a CTA barrier,
+// so the result is deterministic: it is the same top-L queue the sequential
+// definition produces, whatever order the warps touch it in.
+//
+// Per step, inside one CTA:
+//   select   warp 0 takes the first min(M_s, #unchecked) unchecked entries of
+//            the sorted queue by ballot + popc and marks them checked;
+//   expand   all threads read the M adjacency rows (coalesced int32 rows) and
+//            insert each neighbour into the shared-memory visited table;
+//            survivors get a slot in the candidate buffer (warp-aggregated
+//            atomics);
+//   distance teams of lanes gather the candidates' rows with 16-byte
+//            non-caching loads and reduce partial sums with shuffles;
+//   sort     bitonic sort of the packed (key, id) candidates;
+//   merge    drop candidates whose id is already queued (only possible after
+//            the visited table forgot a vertex), then a rank-based parallel
+//            merge of the queue and the candidates, truncated to L.
+// The visited table is reset to the queue's ids when it is half full; the
+// queue is then still the top-L of everything seen (a forgotten vertex that
+// is met again either duplicates a queued id, which the merge drops, or ranks
+// below the L-th entry again), so ids are unchanged and only the distance
+// count grows.
+#include "search_common.cuh"
+
+namespace ann {
+
+struct Ctrl {
+    int nact;
+    int ncand;
+    int qlen;
+    int hash_count;
+    int anydup;
+    long long qi;
+};
+
+template <int NT, int STORE>
+__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(const SearchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Ctrl ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M);
+    float *qv = reinterpret_cast<float *>(smem + lay.q_off);
+    entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
+    entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
+    entry_t *cand = reinterpret_cast<entry_t *>(smem + lay.cand_off);
+    unsigned char *dup = smem + lay.dup_off;
+    uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
+    int *act = reinterpret_cast<int *>(smem + lay.act_off);
+    const int H = 1 << a.hash_bits;
+    const int R = a.R;
+
+    for (;;) {
+        if (tid == 0) {
+            long long qi = a.persistent ? (long long)atomicAdd(a.work_counter, 1) : (long long)blockIdx.x;
+            ctl.qi = qi;
+        }
+        __syncthreads();
+        const long long qi = ctl.qi;
+        if (qi >= a.nq) break;
+        const int64_t t0 = global_ns();
+
+        const int k = a.k_arr ? a.k_arr[qi] : a.k;
+        const int L = a.L_arr ? a.L_arr[qi] : a.L;
+        const int Mmax = a.M_arr ? a.M_arr[qi] : a.M;
+        int64_t *oid = a.out_ids + (size_t)qi * a.k;
+        float *odist = a.out_dists + (size_t)qi * a.k;
+        const bool bad = k < 1 || k > a.k || L < k || L > a.L || Mmax < 1 || Mmax > a.M;
+        if (bad) {
+            for (int i = tid; i < a.k; i += NT) {
+                oid[i] = -1;
+                odist[i] = __int_as_float(0x7f800000);
+            }
+            if (tid == 0 && a.stats) {
+                ann_query_stats st = {};
+                st.steps = -1;
+                a.stats[qi] = st;
+            }
+            if (!a.persistent) break;
+            __syncthreads();
+            continue;
+        }
+
+        // query into shared memory, zero padded; clear the visited table
+        const float *qg = a.queries + (size_t)qi * a.d;
+        for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
+        for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
+        if (tid == 0) cand[0] = (entry_t)(uint32_t)a.entry;
+        __syncthreads();
+        // the entry point P: distance, queue = [P], visited = {P}
+        compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, 1);
+        __syncthreads();
+        if (tid == 0) {
+            Qa[0] = cand[0];
+            visited_insert(table, a.hash_bits, (uint32_t)a.entry);
+            ctl.qlen = 1;
+            ctl.hash_count = 1;
+        }
+        __syncthreads();
+
+        long long steps = 0, expansions = 0, evals = 1, resets = 0, dropped = 0;
+        int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
+        entry_t *Q = Qa, *Qn = Qb;
+        for (;;) {
+            int qlen = ctl.qlen;
+            // --- forget the visited table when half full (keep the queued ids)
+            if (ctl.hash_count * 2 > H) {
+                for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
+                __syncthreads();
+                for (int i = tid; i < qlen; i += NT) visited_insert(table, a.hash_bits, entry_id(Q[i]));
+                if (tid == 0) ctl.hash_count = qlen;
+                resets++;
+            }
+            // --- select the first Mcur unchecked entries (rank order) and mark them
+            if (warp == 0) {
+                int found = 0;
+                for (int b = 0; b < qlen && found < Mcur; b += 32) {
+                    const int i = b + lane;
+                    entry_t e = i < qlen ? Q[i] : kChecked;
+                    const bool un = !(e & kChecked);
+                    const unsigned bal = __ballot_sync(kFull, un);
+                    const int r = found + __popc(bal & ((1u << lane) - 1u));
+                    if (un && r < Mcur) {
+                        act[r] = (int)entry_id(e);
+                        Q[i] = e | kChecked;
+                    }
+                    found += __popc(bal);
+                }
+                if (lane == 0) {
+                    ctl.nact = found < Mcur ? found : Mcur;
+                    ctl.ncand = 0;
+                    ctl.anydup = 0;
+                }
+            }
+            __syncthreads();
+            const int nact = ctl.nact;
+            if (nact == 0) break;  // no unchecked vertex left
+            steps++;
+            expansions += nact;
+
+            // --- expand: adjacency rows -> visited filter -> candidate ids
+            const int total = nact * R;
+            for (int b = warp * 32; b < total; b += NT) {
+                const int i = b + lane;
+                int u = -1;
+                if (i < total) {
+                    const int aidx = i / R, r = i - aidx * R;
+                    u = __ldg(a.adj + (size_t)act[aidx] * R + r);
+                }
+                const bool fresh = u >= 0 && visited_insert(table, a.hash_bits, (uint32_t)u) != 0;
+                const unsigned bal = __ballot_sync(kFull, fresh);
+                int basepos = 0;
+                if (lane == 0 && bal) basepos = atomicAdd(&ctl.ncand, __popc(bal));
+                basepos = __shfl_sync(kFull, basepos, 0);
+                if (fresh) cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+            }
+            __syncthreads();
+            const int nc = ctl.ncand;
+            if (tid == 0) ctl.hash_count += nc;
+            evals += nc;
+            if (nc > 0) {
+                // --- distances
+                compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc);
+                int P = 32;
+                while (P < nc) P <<= 1;
+                for (int i = nc + tid; i < P; i += NT) cand[i] = kEmptyEntry;
+                __syncthreads();
+                // --- sort the candidates by (key, id)
+                block_bitonic_sort<NT>(cand, P);
+                // --- drop ids already queued or repeated in this step
+                int any = 0;
+                for (int j = tid; j < nc; j += NT) {
+                    const entry_t c = cand[j];
+                    bool d = (j > 0 && cand[j - 1] == c);
+                    if (!d) {
+                        const int pos = count_below(Q, qlen, c);
+                        d = pos < qlen && (Q[pos] & kMask) == c;
+                    }
+                    dup[j] = d;
+                    any |= d;
+                }
+                int ncl = nc;
+                if (__syncthreads_or(any)) {
+                    if (warp == 0) {
+                        int out = 0;
+                        for (int b = 0; b < nc; b += 32) {
+                            const int j = b + lane;
+                            const bool keep = j < nc && !dup[j];
+                            const entry_t c = j < nc ? cand[j] : 0ull;
+                            const unsigned bal = __ballot_sync(kFull, keep);
+                            if (keep) cand[out + __popc(bal & ((1u << lane) - 1u))] = c;
+                            out += __popc(bal);
+                        }
+                        if (lane == 0) ctl.anydup = out;
+                    }
+                    __syncthreads();
+                    ncl = ctl.anydup;
+                    dropped += nc - ncl;
+                }
+                // --- merge queue and candidates by rank, truncate to L
+                for (int i = tid; i < qlen; i += NT) {
+                    const entry_t e = Q[i];
+                    const int pos = i + count_below(cand, ncl, e & kMask);
+                    if (pos < L) Qn[pos] = e;
+                }
+                for (int j = tid; j < ncl; j += NT) {
+                    const entry_t c = cand[j];
+                    const int pos = j + count_below(Q, qlen, c);
+                    if (pos < L) Qn[pos] = c;
+                }
+                __syncthreads();
+                if (tid == 0) ctl.qlen = min(L, qlen + ncl);
+                entry_t *tmp = Q;
+                Q = Qn;
+                Qn = tmp;
+            }
+            __syncthreads();
+            if (steps % a.t == 0) Mcur = min(2 * Mcur, Mmax);
+        }
+
+        // --- output: first k of the queue, optionally re-ranked with FP32 rows
+        const int qlen = ctl.qlen;
+        const entry_t *res = Q;
+        if (a.rerank) {
+            for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
+            __syncthreads();
+            compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
+            int P = 32;
+            while (P < qlen) P <<= 1;
+            for (int i = qlen + tid; i < P; i += NT) cand[i] = kEmptyEntry;
+            __syncthreads();
+            block_bitonic_sort<NT>(cand, P);
+            res = cand;
+        }
+        for (int i = tid; i < k; i += NT) {
+            if (i < qlen) {
+                oid[i] = (int64_t)entry_id(res[i]);
+                odist[i] = entry_key(res[i]);
+            } else {
+                oid[i] = -1;
+                odist[i] = __int_as_float(0x7f800000);
+            }
+        }
+        for (int i = k + tid; i < a.k; i += NT) {
+            oid[i] = -1;
+            odist[i] = __int_as_float(0x7f800000);
+        }
+        if (tid == 0 && a.stats) {
+            ann_query_stats st;
+            st.steps = steps;
+            st.expansions = expansions;
+            st.evals = evals;
+            st.hash_resets = resets;
+            st.dup_dropped = dropped;
+            st.merges = 0;
+            st.t_start_ns = t0;
+            st.t_end_ns = global_ns();
+            a.stats[qi] = st;
+        }
+        if (!a.persistent) break;
+        __syncthreads();
+    }
+}
+
+template <int NT, int STORE>
+static cudaError_t launch_t(const SearchArgs &a, int smem, int grid, cudaStream_t s) {
+    auto fn = sync_search_kernel<NT, STORE>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT, int STORE>
+static cudaError_t occ_t(int smem, int *bps) {
+    auto fn = sync_search_kernel<NT, STORE>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, NT, smem);
+}
+
+#define ANN_DISPATCH_STORE(NT, FN, ...)                                          \
+    switch (storage) {                                                           \
+        case ANN_STORE_F32: return FN<NT, ANN_STORE_F32>(__VA_ARGS__);           \
+        case ANN_STORE_BF16: return FN<NT, ANN_STORE_BF16>(__VA_ARGS__);         \
+        case ANN_STORE_F16: return FN<NT, ANN_STORE_F16>(__VA_ARGS__);           \
+        case ANN_STORE_E4M3: return FN<NT, ANN_STORE_E4M3>(__VA_ARGS__);         \
+    }                                                                            \
+    return cudaErrorInvalidValue;
+
+template <int NT>
+static cudaError_t launch_nt(const SearchArgs &a, int storage, int smem, int grid, cudaStream_t s) {
+    ANN_DISPATCH_STORE(NT, launch_t, a, smem, grid, s)
+}
+template <int NT>
+static cudaError_t occ_nt(int storage, int smem, int *bps) {
+    ANN_DISPATCH_STORE(NT, occ_t, smem, bps)
+}
+
+cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, int smem, int grid,
+                               cudaStream_t s) {
+    switch (threads) {
+        case 64: return launch_nt<64>(a, storage, smem, grid, s);
+        case 128: return launch_nt<128>(a, storage, smem, grid, s);
+        case 256: return launch_nt<256>(a, storage, smem, grid, s);
+        case 512: return launch_nt<512>(a, storage, smem, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t sync_search_occupancy(int storage, int threads, int smem, int *bps) {
+    switch (threads) {
+        case 64: return occ_nt<64>(storage, smem, bps);
+        case 128: return occ_nt<128>(storage, smem, bps);
+        case 256: return occ_nt<256>(storage, smem, bps);
+        case 512: return occ_nt<512>(storage, smem, bps);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ann

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every function include/ann.h
+declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ann.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ann_[a-z_0-9]+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("ann_index_create", "ann_index_destroy", "ann_search", "ann_search_ex",
+                 "ann_search_host", "ann_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2201_13007_gb300 import _build
+    path = _build.build()
+    out = subprocess.check_output(["nm", "-D", "--defined-only", path], text=True)
+    exported = set(l.split()[-1] for l in out.splitlines() if " T " in l)
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_header_compiles_as_c():
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-x", "c",
+                        os.path.join(ROOT, "include", "ann.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_argument_errors_without_gpu():
+    """Calls rejected on the host before any CUDA work."""
+    import paper_2201_13007_gb300 as ann
+    with pytest.raises(ann.AnnError):
+        ann.ann_index_create(None, 10, 4, 0, None, 2, 0, 0, 0)
+    assert "NULL" in ann.ann_last_error()
+    with pytest.raises(ann.AnnError):
+        ann.ann_search(None, None, 1, 1, 1, 1, None, None, None)

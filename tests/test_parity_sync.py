@@ -1,0 +1,232 @@
+"""GPU parity of the synchronous top-M search kernel against the FP64 oracle,
+called through the C ABI (libann.so via ctypes)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2201_13007_gb300 import synth  # noqa: E402
+from parity_util import compare_exact, compare_float  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ann():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_13007_gb300 as pkg
+    from paper_2201_13007_gb300.index import Index, stats_dict
+    return pkg, Index, stats_dict
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.make_workload("tiny", 10000, 100)
+
+
+@pytest.fixture(scope="module")
+def sift_small():
+    return synth.make_workload("sift", 20000, 64)
+
+
+def _run(Index, w, storage="f32", keep_f32=False, k=10, L=64, M=4, queries=None, **kw):
+    ix = Index(w.base, w.adj, w.entry, storage=storage, metric=w.metric, keep_f32=keep_f32)
+    q = torch.from_numpy(queries if queries is not None else w.queries).cuda()
+    ids, dists, st = ix.search(q, k, L, M, with_stats=True, **kw)
+    torch.cuda.synchronize()
+    out = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
+    ix.close()
+    return out
+
+
+@pytest.mark.parametrize("L", [32, 64, 128])
+@pytest.mark.parametrize("M", [1, 4])
+def test_tiny_float_parity(ann, oracle_mod, tiny, L, M):
+    """Config: 10,000 x 32 FP32 mixture, exact 16-NN + reverse edges (cap 24),
+    100 queries, k = 10, one CTA per query."""
+    _, Index, stats_dict = ann
+    ids, dists, st = _run(Index, tiny, L=L, M=M, hash_bits=15)
+    o_ids, o_keys, o_st = oracle_mod.search(tiny.base, tiny.adj, tiny.entry, tiny.queries, algo="topm",
+                                            L=L, K=10, M0=1, M_max=M, t=1, nthreads=8)
+    rep = compare_float(ids, dists, o_ids, o_keys, o_st["tie_events"], tiny.base, tiny.queries, "l2")
+    s = stats_dict(st)
+    clean = (o_st["tie_events"] == 0)
+    assert (s["hash_resets"] == 0).all()
+    # with no forgotten vertices the distance count is exactly |V| of the oracle
+    np.testing.assert_array_equal(s["evals"][clean], o_st["evals"][clean])
+    np.testing.assert_array_equal(s["steps"][clean], o_st["steps"][clean])
+    assert rep["tie_free"] >= 90
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("L,M", [(16, 1), (64, 2), (100, 8), (200, 16), (64, 32)])
+def test_integer_data_bit_exact(ann, oracle_mod, sift_small, storage, L, M):
+    """0..255 integer vectors, d = 128: FP32 sums are exact, so ids and keys
+    must equal the oracle's bit for bit (BF16 holds 0..255 exactly)."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15)
+    o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
+                                            M0=1, M_max=M, t=1, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+    s = stats_dict(st)
+    np.testing.assert_array_equal(s["evals"], o_st["evals"])
+    np.testing.assert_array_equal(s["steps"], o_st["steps"])
+    np.testing.assert_array_equal(s["expansions"], o_st["expansions"])
+
+
+@pytest.mark.parametrize("hash_bits", [8, 9, 11])
+def test_forgetful_visited_table_keeps_ids(ann, oracle_mod, sift_small, hash_bits):
+    """A small visited table is reset many times per query; ids and keys stay
+    exact (the merge drops re-found queued ids), only evals grow."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits)
+    o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
+                                            M0=1, M_max=8, t=1, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+    s = stats_dict(st)
+    assert (s["hash_resets"] > 0).any()
+    assert (s["evals"] >= o_st["evals"]).all()
+
+
+@pytest.mark.parametrize("M0,t", [(1, 2), (2, 1), (4, 3)])
+def test_schedule_variants(ann, oracle_mod, sift_small, M0, t):
+    _, Index, _ = ann
+    w = sift_small
+    ids, dists, _ = _run(Index, w, L=96, M=16, M0=M0, t=t, hash_bits=15)
+    o_ids, o_keys, _ = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=96, K=10,
+                                         M0=M0, M_max=16, t=t, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+def test_block_sizes_agree(ann, oracle_mod, sift_small, threads):
+    _, Index, _ = ann
+    w = sift_small
+    ids, dists, _ = _run(Index, w, L=64, M=8, threads=threads)
+    o_ids, o_keys, _ = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=64, K=10,
+                                         M0=1, M_max=8, t=1, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+
+
+def test_ip_metric_parity(ann, oracle_mod):
+    _, Index, _ = ann
+    w = synth.make_workload("deep", 20000, 64, components=32)
+    ids, dists, st = _run(Index, w, L=64, M=4, hash_bits=15)
+    o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", metric="ip",
+                                            L=64, K=10, M0=1, M_max=4, t=1, nthreads=8)
+    compare_float(ids, dists, o_ids, o_keys, o_st["tie_events"], w.base, w.queries, "ip")
+
+
+def test_edge_cases_small_graphs(ann, oracle_mod):
+    """L = 1, k = L, L > n (queue never fills), -1 padded rows, unreachable
+    vertices, duplicate vectors (exact key ties broken by id), ragged d."""
+    _, Index, _ = ann
+    for seed, (n, d, R, pad, dup) in enumerate([(50, 3, 4, 0.3, 0.2), (300, 37, 7, 0.1, 0.1),
+                                                 (9, 5, 2, 0.5, 0.0), (1, 4, 1, 0.0, 0.0)]):
+        base, adj, q = synth.random_graph(max(n, 2), d, R, seed=seed, nq=16, pad_frac=pad, dup_frac=dup)
+        base, adj = base[:n], np.where(adj[:n] < n, adj[:n], -1).astype(np.int32)
+        # integer-valued copies make the comparison exact
+        base = np.rint(base * 8).astype(np.float32)
+        q = np.rint(q * 8).astype(np.float32)
+        w = synth.Workload("edge", base, q, adj, 0, "l2")
+        for k, L, M in [(1, 1, 1), (3, 3, 2), (5, 64, 4), (2, 8, 64)]:
+            ids, dists, _ = _run(Index, w, k=k, L=L, M=M, queries=q)
+            o_ids, o_keys, _ = oracle_mod.search(base, adj, 0, q, algo="topm", L=L, K=k, M0=1, M_max=M, t=1)
+            compare_exact(ids, dists, o_ids, o_keys)
+
+
+def test_empty_batch_and_argument_errors(ann, tiny):
+    pkg, Index, _ = ann
+    ix = Index(tiny.base, tiny.adj, tiny.entry)
+    q = torch.zeros((0, tiny.d), device="cuda")
+    ids, dists = ix.search(q, 10, 32, 4)
+    assert ids.shape == (0, 10)
+    qq = torch.zeros((2, tiny.d), device="cuda")
+    with pytest.raises(pkg.AnnError):
+        ix.search(qq, 11, 10, 1)  # k > L
+    with pytest.raises(pkg.AnnError):
+        ix.search(qq, 1, 4096, 1)  # L too large
+    with pytest.raises(pkg.AnnError):
+        ix.search(qq, 1, 8, 65)  # M too large
+    ix.search(qq, 1, 8, 1, rerank=True)  # an FP32 base is its own re-rank copy
+    ix.close()
+    ixb = Index(tiny.base, tiny.adj, tiny.entry, storage="bf16")
+    with pytest.raises(pkg.AnnError):
+        ixb.search(qq, 1, 8, 1, rerank=True)  # no FP32 copy kept
+    ixb.close()
+
+
+def test_bad_adjacency_rejected(ann):
+    pkg, Index, _ = ann
+    base = np.zeros((4, 8), np.float32)
+    adj = np.array([[1], [2], [7], [0]], np.int32)
+    with pytest.raises(pkg.AnnError):
+        Index(base, adj, 0)
+    with pytest.raises(pkg.AnnError):
+        Index(torch.from_numpy(base).cuda(), torch.from_numpy(adj).cuda(), 0)
+
+
+def test_persistent_per_query_and_host_paths_agree(ann, sift_small):
+    _, Index, _ = ann
+    w = sift_small
+    ix = Index(w.base, w.adj, w.entry)
+    q = torch.from_numpy(w.queries).cuda()
+    ids0, d0 = ix.search(q, 10, 80, 8)
+    ids1, d1 = ix.search(q, 10, 80, 8, persistent=True)
+    assert torch.equal(ids0, ids1) and torch.equal(d0, d1)
+    hi, hd = ix.search_host(torch.from_numpy(w.queries).pin_memory(), 10, 80, 8)
+    assert torch.equal(hi, ids0.cpu()) and torch.equal(hd, d0.cpu())
+    # per-query k / L / M: each row equals its own uniform call
+    nq = q.shape[0]
+    g = np.random.default_rng(0)
+    ks = g.choice([1, 5, 10], nq).astype(np.int32)
+    Ls = np.maximum(ks, g.choice([16, 40, 80], nq)).astype(np.int32)
+    Ms = g.choice([1, 2, 8], nq).astype(np.int32)
+    ids2, d2 = ix.search(q, 10, 80, 8, k_per_query=torch.from_numpy(ks).cuda(),
+                         L_per_query=torch.from_numpy(Ls).cuda(), M_per_query=torch.from_numpy(Ms).cuda(),
+                         persistent=True)
+    ids2, d2 = ids2.cpu(), d2.cpu()
+    for i in range(nq):
+        a, b = ix.search(q[i:i + 1], int(ks[i]), int(Ls[i]), int(Ms[i]))
+        assert torch.equal(ids2[i, :ks[i]], a[0].cpu()) and torch.equal(d2[i, :ks[i]], b[0].cpu())
+        assert (ids2[i, ks[i]:] == -1).all()
+    ix.close()
+
+
+def test_deterministic_reruns(ann, tiny):
+    _, Index, _ = ann
+    ix = Index(tiny.base, tiny.adj, tiny.entry)
+    q = torch.from_numpy(tiny.queries).cuda()
+    ref = ix.search(q, 10, 128, 4, hash_bits=9)
+    for _ in range(20):
+        got = ix.search(q, 10, 128, 4, hash_bits=9)
+        assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+    ix.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16", "e4m3"])
+def test_reduced_precision_with_rerank(ann, oracle_mod, storage):
+    """Reduced-precision storage: the search must follow the oracle run on
+    the stored (rounded) values; the re-rank must equal the oracle's exact
+    re-rank of that final queue with FP32 rows."""
+    _, Index, _ = ann
+    w = synth.make_workload("gist", 8000, 48, d=240)
+    L, M = 64, 4
+    stored = oracle_mod.stored_values(w.base, storage)
+    ix = Index(w.base, w.adj, w.entry, storage=storage, keep_f32=True)
+    q = torch.from_numpy(w.queries).cuda()
+    ids_nr, d_nr = ix.search(q, L, L, M, hash_bits=15)          # whole final queue, stored keys
+    ids_rr, d_rr = ix.search(q, 10, L, M, hash_bits=15, rerank=True)
+    torch.cuda.synchronize()
+    o_ids, o_keys, o_st = oracle_mod.search(stored, w.adj, w.entry, w.queries, algo="topm", L=L, K=L,
+                                            M0=1, M_max=M, t=1, nthreads=8)
+    compare_float(ids_nr.cpu().numpy(), d_nr.cpu().numpy(), o_ids, o_keys, o_st["tie_events"], stored,
+                  w.queries, "l2")
+    clean = o_st["tie_events"] == 0
+    r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, o_ids, 10)
+    compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
+                  np.zeros(clean.sum()), w.base, w.queries[clean], "l2")
+    ix.close()
