@@ -60,6 +60,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def log(*a):
+    print(f"[bench {time.strftime('%H:%M:%S')}]", *a, file=sys.stderr, flush=True)
+
+
 def recall_at_k(ids, gt):
     hits = 0
     for a, b in zip(ids, gt):
@@ -171,7 +175,9 @@ def run_ours(args):
 
     t_setup = time.time()
     w = synth.make_workload("sift", args.n, args.nq)
+    log(f"workload ready in {time.time() - t_setup:.1f}s (repaired links {w.meta['repaired_links']})")
     gt = exact_topk_gpu(w.base, w.queries, K, torch)
+    log("ground truth ready")
     ix32 = Index(w.base, w.adj, w.entry, storage="f32")
     ix16 = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True)
     q = torch.from_numpy(w.queries).cuda()
@@ -198,6 +204,7 @@ def run_ours(args):
                 sweep[(name, L, M)] = (rec, dt)
                 if rec >= max(TARGETS) + 0.003:
                     break
+            log(f"sweep {name} M={M}: last L={L} recall={rec:.4f} {dt * 1e3:.1f} ms")
     points = {}
     for name in forms:
         for tgt in TARGETS:
@@ -206,6 +213,7 @@ def run_ours(args):
                 dt, L, M, rec = min(ok)
                 points[(name, tgt)] = (L, M)
     setup_s = time.time() - t_setup
+    log("operating points", points)
 
     # ---- timed steps
     def timed(ix, kw, L, M, steps, warmup):

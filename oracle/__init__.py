@@ -61,7 +61,8 @@ class Graph(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("K", ctypes.c_int32), ("M0", ctypes.c_int32),
                 ("M_max", ctypes.c_int32), ("t", ctypes.c_int32), ("R_ratio", ctypes.c_double),
-                ("max_steps", ctypes.c_int64), ("tie_tol", ctypes.c_double)]
+                ("max_steps", ctypes.c_int64), ("tie_tol", ctypes.c_double),
+                ("tie_abs", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -121,9 +122,10 @@ def _graph(base, adj, entry, metric):
     return g, (base, adj)
 
 
-def _params(L, K, M0=1, M_max=1, t=1, R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5):
+def _params(L, K, M0=1, M_max=1, t=1, R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0):
     return Params(L=int(L), K=int(K), M0=int(M0), M_max=int(M_max), t=int(t),
-                  R_ratio=float(R_ratio), max_steps=int(max_steps), tie_tol=float(tie_tol))
+                  R_ratio=float(R_ratio), max_steps=int(max_steps), tie_tol=float(tie_tol),
+                  tie_abs=float(tie_abs))
 
 
 def _check(rc, what):
@@ -132,7 +134,7 @@ def _check(rc, what):
 
 
 def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M_max=1, t=1,
-           R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, nthreads=1):
+           R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0, nthreads=1):
     """Run one of the paper's searches for every query. Returns (ids int64
     nq x K, keys float64 nq x K, stats structured array nq)."""
     g, keep = _graph(base, adj, entry, metric)
@@ -143,7 +145,7 @@ def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M
     ids = np.empty((nq, K), np.int64)
     keys = np.empty((nq, K), np.float64)
     st = np.zeros(nq, _STATS_DTYPE)
-    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol)
+    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs)
     rc = lib().orc_search(ALGOS[algo], ctypes.byref(g), ctypes.byref(p), _ptr(q), nq,
                           _ptr(ids), _ptr(keys), _ptr(st), int(nthreads))
     _check(rc, "search")
@@ -152,7 +154,7 @@ def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M
 
 
 def search_trace(base, adj, entry, query, *, algo="topm", metric="l2", L, K, M0=1, M_max=1, t=1,
-                 R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5):
+                 R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0):
     """One query with its full final state: dict with ids, keys, stats, the
     final queue (ids, keys, checked), the visited set in visit order and the
     expansion order."""
@@ -171,7 +173,7 @@ def search_trace(base, adj, entry, query, *, algo="topm", metric="l2", L, K, M0=
     ids = np.empty(K, np.int64)
     keys = np.empty(K, np.float64)
     st = Stats()
-    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol)
+    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs)
     rc = lib().orc_search_trace(ALGOS[algo], ctypes.byref(g), ctypes.byref(p), _ptr(q), _ptr(ids),
                                 _ptr(keys), ctypes.byref(st), ctypes.byref(tr))
     _check(rc, "search_trace")

@@ -77,6 +77,7 @@ typedef struct {
     double R_ratio;    /* Alg. 2 position ratio; INFINITY = never merge early */
     int64_t max_steps; /* stop after this many steps; < 0 = run to convergence */
     double tie_tol;    /* relative gap under which a boundary decision is logged */
+    double tie_abs;    /* plus this absolute gap (inner-product keys can be near zero) */
 } orc_params;
 
 typedef struct {
@@ -141,12 +142,12 @@ static int entry_cmp(const void *pa, const void *pb) {
     return 0;
 }
 
-static int near_tie(double a, double b, double tol) {
+static int near_tie_abs(double a, double b, double tol, double abs_tol) {
     double gap = fabs(b - a);
     double scale = fmax(fabs(a), fabs(b));
-    if (scale == 0.0) return 1;
-    return gap < tol * scale;
+    return gap <= tol * scale + abs_tol;
 }
+#define near_tie(a, b, tol) near_tie_abs((a), (b), (tol), p->tie_abs)
 
 /* Insert e into the sorted array q[0..*len) keeping (key, id) order. */
 static void insert_sorted(entry_t *q, int32_t *len, entry_t e) {

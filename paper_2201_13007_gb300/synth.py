@@ -282,59 +282,66 @@ def reachable_from(adj: np.ndarray, entry: int) -> np.ndarray:
     return mask
 
 
+def _nearest_among(x, targets, pool):
+    """For each row index in ``targets``, the index in ``pool`` of the nearest
+    point by L2 (chunked GEMM on the torch device)."""
+    import torch
+    dev = _torch_device()
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        T = torch.from_numpy(np.ascontiguousarray(x[targets])).to(dev, torch.float32)
+        tn = (T * T).sum(1)
+        best_d = torch.full((T.shape[0],), float("inf"), device=dev)
+        best_i = torch.zeros(T.shape[0], dtype=torch.int64, device=dev)
+        step = 1 << 18
+        for a in range(0, pool.shape[0], step):
+            P = torch.from_numpy(np.ascontiguousarray(x[pool[a:a + step]])).to(dev, torch.float32)
+            D = tn[:, None] + (P * P).sum(1)[None, :] - 2.0 * (T @ P.T)
+            v, i = D.min(1)
+            upd = v < best_d
+            best_d = torch.where(upd, v, best_d)
+            best_i = torch.where(upd, i + a, best_i)
+        return pool[best_i.cpu().numpy()]
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def repair_reachability(adj: np.ndarray, entry: int, knn: np.ndarray, x: np.ndarray,
-                        max_rounds: int = 4096):
-    """Make every vertex reachable from ``entry``. Each round links the
-    unreachable vertices that have a reachable k-NN neighbour from the nearest
-    such neighbour; if none has one, the unreachable vertex nearest to the
-    reachable set (FP64 L2, brute force) is linked from its nearest reachable
-    vertex. A link takes a free slot if there is one, else the last slot not
-    already holding a link added here. Returns (adj, number of links added)."""
+                        max_rounds: int = 256, per_round: int = 1024):
+    """Make every vertex reachable from ``entry``. Each round finds the
+    unreachable set by BFS and links up to ``per_round`` of its vertices
+    (evenly spaced by id) from their nearest reachable vertex that still has
+    room (a free slot, else one of its last slots; at most R/2 slots of a row
+    are given to such links); a link makes the whole part of the graph behind
+    that vertex reachable. Returns (adj, number of links added)."""
     adj = adj.copy()
     n, R = adj.shape
     protected = np.zeros((n, R), bool)
     added = 0
-
-    def link(src, u):
-        nonlocal added
-        row = adj[src]
-        if u in row:
-            return
-        free = np.flatnonzero(row < 0)
-        if free.size:
-            slot = int(free[0])
-        else:
-            cand = np.flatnonzero(~protected[src])
-            if cand.size == 0:
-                return
-            slot = int(cand[-1])
-        row[slot] = u
-        protected[src, slot] = True
-        added += 1
-
     for _ in range(max_rounds):
         mask = reachable_from(adj, entry)
         un = np.flatnonzero(~mask)
         if un.size == 0:
             return adj, added
-        progressed = False
-        for u in un:
-            for v in knn[u]:
-                if v >= 0 and mask[v]:
-                    link(int(v), int(u))
-                    progressed = True
-                    break
-        if not progressed:
-            reach = np.flatnonzero(mask)
-            xr = x[reach].astype(np.float64)
-            best = (np.inf, -1, -1)
-            for u in un[: min(un.size, 256)]:
-                diff = xr - x[u].astype(np.float64)
-                dd = np.einsum("ij,ij->i", diff, diff)
-                i = int(np.argmin(dd))
-                if dd[i] < best[0]:
-                    best = (float(dd[i]), int(reach[i]), int(u))
-            link(best[1], best[2])
+        pick = un[np.linspace(0, un.size - 1, min(per_round, un.size)).astype(np.int64)]
+        pick = np.unique(pick)
+        room = mask & (protected.sum(1) < max(1, R // 2))
+        if not room.any():
+            break
+        src = _nearest_among(x, pick, np.flatnonzero(room))
+        for s_, u in zip(src.tolist(), pick.tolist()):
+            row = adj[s_]
+            if u in row or protected[s_].sum() >= max(1, R // 2):
+                continue
+            free = np.flatnonzero(row < 0)
+            if free.size:
+                slot = int(free[0])
+            else:
+                slot = int(np.flatnonzero(~protected[s_])[-1])
+            row[slot] = u
+            protected[s_, slot] = True
+            added += 1
     raise RuntimeError("graph repair did not converge")
 
 
@@ -374,7 +381,7 @@ def _load_or_build(spec: dict, fn):
 def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | None = None,
                   components: int | None = None, cache: bool = True) -> Workload:
     """Build (or load from the cache) a seeded workload of the given shape."""
-    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 1}
+    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 2}
 
     def gen():
         if kind == "tiny":
