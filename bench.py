@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--point", default=None,
+                    help="L,M: skip the recall sweep and time this operating point for every form")
+    ap.add_argument("--forms", default="batched_bf16_rerank,plain_f32")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-single", action="store_true")
     return ap.parse_args()
 
 
@@ -188,10 +194,14 @@ def run_ours(args):
         "batched_bf16_rerank": (ix16, dict(rerank=True, persistent=True), 2),
         "plain_f32": (ix32, dict(), 4),
     }
+    forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
+    head_name = next(iter(forms))
 
     # ---- operating points: cheapest (L, M) reaching each recall target
     sweep = {}
     for name, (ix, kw, _) in forms.items():
+        if args.point:
+            break
         for M in M_SWEEP:
             for L in L_SWEEP:
                 ids, _ = ix.search(q, K, L, M, **kw)
@@ -208,10 +218,16 @@ def run_ours(args):
     points = {}
     for name in forms:
         for tgt in TARGETS:
-            ok = [(dt, L, M, rec) for (nm, L, M), (rec, dt) in sweep.items() if nm == name and rec >= tgt]
-            if ok:
-                dt, L, M, rec = min(ok)
+            if args.point:
+                L, M = (int(v) for v in args.point.split(","))
                 points[(name, tgt)] = (L, M)
+                continue
+            ok = [(dt, L, M, rec) for (nm, L, M), (rec, dt) in sweep.items() if nm == name and rec >= tgt]
+            if not ok:  # target out of reach: take the highest-recall point and report its recall
+                best = max(((rec, -dt, L, M) for (nm, L, M), (rec, dt) in sweep.items() if nm == name))
+                ok = [(0.0, best[2], best[3], best[0])]
+            dt, L, M, rec = min(ok)
+            points[(name, tgt)] = (L, M)
     setup_s = time.time() - t_setup
     log("operating points", points)
 
@@ -241,7 +257,7 @@ def run_ours(args):
         return times, ids.cpu().numpy(), stats.cpu().numpy()
 
     results = {}
-    head = ("batched_bf16_rerank", 0.99)
+    head = (head_name, 0.99)
     with ClockSampler(local) as clk:
         for (name, tgt), (L, M) in points.items():
             ix, kw, es = forms[name]
@@ -266,7 +282,7 @@ def run_ours(args):
     # ---- plain one query per launch (latency form) on a subset
     single = {}
     for tgt in TARGETS:
-        if ("plain_f32", tgt) not in points:
+        if args.skip_single or ("plain_f32", tgt) not in points:
             continue
         L, M = points[("plain_f32", tgt)]
         lat = []
@@ -287,17 +303,17 @@ def run_ours(args):
     hids = torch.empty((nq, K), dtype=torch.int64).pin_memory()
     hd = torch.empty((nq, K), dtype=torch.float32).pin_memory()
     ix, kw, _ = forms[head[0]]
-    for _ in range(args.warmup):
+    for _ in range(0 if args.skip_e2e else args.warmup):
         ix.search_host(hq, K, L, M, out=(hids, hd), **kw)
     e2e_t = []
     barrier()
-    for _ in range(args.steps):
+    for _ in range(0 if args.skip_e2e else args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ix.search_host(hq, K, L, M, out=(hids, hd), **kw)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
+    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
     if dist is not None:
         tt = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -305,7 +321,7 @@ def run_ours(args):
 
     # ---- CPU baseline: the oracle as it stands, bounded sample, rank 0 at N = 1
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(w, L, M, args.cpu_seconds)
 
     if rank != 0:
@@ -329,7 +345,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": h["gbs"], "peak": hbm, "unit": "GB/s",
                      "frac": h["gbs"] / hbm, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "traffic": None,
-                     "kernel": "sync_search_kernel<256, BF16> (persistent)",
+                     "kernel": f"sync_search_kernel<{256 if h['M'] * w.R >= 256 else 128}, "
+                               f"{'BF16' if head[0].startswith('batched') else 'F32'}>",
                      "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 (re-rank) + d*4 + k*12"},
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * w.d * 4,
                 "d2h_bytes_per_step": nq * K * 12},
