@@ -96,9 +96,10 @@ typedef struct {
     int32_t mode;       /* ann_mode; default ANN_MODE_SYNC */
     int32_t M0;         /* initial expansion width; 0 = 1 (Algorithm 3 starts at M = 1) */
     int32_t t;          /* sync mode: M doubles every t steps; 0 = 1 (Sec. 4.2 example) */
-    float R_ratio;      /* async: Algorithm 2 position ratio; 0 = 0.8; INFINITY = merge only when idle */
+    float R_ratio;      /* async: Algorithm 2 position ratio (the paper uses 0.8 / 0.9); 0 merges at
+                         * the checker's first expansion; INFINITY merges only when every walker is idle */
     int32_t rerank;     /* 1 = recompute the final queue's keys from FP32 rows (needs has_f32) */
-    int32_t threads;    /* threads per CTA: 0 = auto, else 64, 128, 256 or 512 */
+    int32_t threads;    /* threads per CTA: 0 = auto; sync 64..512; async 64..1024 and >= 32*M */
     int32_t hash_bits;  /* log2 slots of the per-query visited table; 0 = auto, else 8..15 */
     int32_t persistent; /* 1 = persistent grid that pulls queries from a device counter */
     /* Per-query settings (device int32 arrays of nq entries, or NULL for the
@@ -136,7 +137,8 @@ int ann_index_get_info(const ann_index *index, ann_index_info *info);
  *   queries    device, nq x d float32 row-major.
  *   k          results per query (the paper's K), 1 <= k <= L.
  *   L          candidate-queue capacity of Algorithm 1, 1 <= L <= 2048.
- *   M          maximum expansion width (the paper's M, capped by T), 1..64.
+ *   M          maximum expansion width (the paper's M, capped by T), 1..64
+ *              (async mode: the number of walkers T, 1..32).
  *   out_ids    device int64 nq x k; out_dists device float nq x k (squared
  *              l2, or -<q,x>). Slots beyond the reachable set hold (-1, +inf).
  * Asynchronous on stream; argument errors return before anything is queued.

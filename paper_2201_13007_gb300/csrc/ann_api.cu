@@ -166,6 +166,8 @@ struct Plan {
     int threads;
     int smem;
     int grid;
+    int mode;
+    int storage;
 };
 
 int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
@@ -180,15 +182,28 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     ann_search_params def;
     memset(&def, 0, sizeof(def));
     if (!p) p = &def;
-    if (p->mode != ANN_MODE_SYNC) return fail(ANN_ERR_ARG, "mode %d is not available in this build", p->mode);
+    if (p->mode != ANN_MODE_SYNC && p->mode != ANN_MODE_ASYNC) return fail(ANN_ERR_ARG, "unknown mode %d", p->mode);
+    const bool async = p->mode == ANN_MODE_ASYNC;
     const int M0 = p->M0 ? p->M0 : 1;
     const int t = p->t ? p->t : 1;
     if (M0 < 1 || t < 1) return fail(ANN_ERR_ARG, "M0=%d and t=%d must be >= 1", M0, t);
     if (p->rerank && !x.base32) return fail(ANN_ERR_ARG, "rerank needs an FP32 copy (ANN_INDEX_KEEP_F32)");
+    if (async && !(p->R_ratio >= 0.f)) return fail(ANN_ERR_ARG, "R_ratio must be >= 0 (or INFINITY)");
+    if (async && M > 32) return fail(ANN_ERR_ARG, "async mode runs one warp per walker: M=%d > 32", M);
     int threads = p->threads;
-    if (threads == 0) threads = (M * x.R >= 256) ? 256 : 128;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
-        return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
+    if (async) {
+        // one warp per walker: T = M walkers, at least two warps
+        int walkers = 2;
+        while (walkers < M) walkers <<= 1;
+        if (threads == 0) threads = 32 * walkers;
+        if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+            return fail(ANN_ERR_ARG, "threads=%d not in {64,...,1024}", threads);
+        if (threads / 32 < M) return fail(ANN_ERR_ARG, "async mode needs threads >= 32*M");
+    } else {
+        if (threads == 0) threads = (M * x.R >= 256) ? 256 : 128;
+        if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+            return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
+    }
     int hb = p->hash_bits;
     if (hb == 0) hb = L > 512 ? 14 : 13;
     if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
@@ -229,16 +244,20 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (a.rerank && L > need) need = L;
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
-    ann::SmemLayout lay = ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M);
-    if (lay.total > max_dyn_smem())
+    int smem = async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, a.hash_bits)
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M).total;
+    if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
-                    lay.total, max_dyn_smem());
+                    smem, max_dyn_smem());
     plan->threads = threads;
-    plan->smem = lay.total;
+    plan->smem = smem;
+    plan->mode = p->mode;
+    plan->storage = x.storage;
     plan->grid = (int)(nq > 0x7fffffff ? 0x7fffffff : nq);
     if (a.persistent && nq > 0) {
         int bps = 0;
-        cudaError_t e = ann::sync_search_occupancy(x.storage, threads, lay.total, &bps);
+        cudaError_t e = async ? ann::async_search_occupancy(x.storage, threads, smem, &bps)
+                              : ann::sync_search_occupancy(x.storage, threads, smem, &bps);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         if (bps < 1) return fail(ANN_ERR_ARG, "kernel does not fit on an SM");
         int64_t g = (int64_t)bps * sm_count();
@@ -253,7 +272,9 @@ int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
     cudaGetDevice(&dev);
     if (dev != index->d.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, index->d.device);
     if (plan.a.persistent) ANN_CUDA(cudaMemsetAsync(index->d.work_counter, 0, sizeof(int), s));
-    cudaError_t e = ann::launch_sync_search(plan.a, index->d.storage, plan.threads, plan.smem, plan.grid, s);
+    cudaError_t e = plan.mode == ANN_MODE_ASYNC
+                        ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
+                        : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "search launch");
     return ANN_OK;
 }

@@ -108,6 +108,12 @@ cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, in
                                int grid, cudaStream_t stream);
 cudaError_t sync_search_occupancy(int storage, int threads, int smem_bytes, int *blocks_per_sm);
 
+// search_async.cu
+cudaError_t launch_async_search(const SearchArgs &a, int storage, int threads, int smem_bytes, int grid,
+                                cudaStream_t stream);
+cudaError_t async_search_occupancy(int storage, int threads, int smem_bytes, int *blocks_per_sm);
+int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits);
+
 // encode.cu
 cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, void *dst, int32_t d_pad,
                           float *scales, cudaStream_t stream);

@@ -280,3 +280,128 @@ __device__ __forceinline__ int64_t global_ns() {
 }
 
 }  // namespace ann
+
+namespace ann {
+
+// Warp-level key computation for the nc <= 32 candidates whose ids sit in the
+// low word of c[0..nc) (a per-warp shared buffer); results are written back
+// packed. Same team layout as compute_keys, one warp only.
+template <int STORE, int U = 4>
+__device__ __forceinline__ void warp_compute_keys(const void *rows, const float *scales, int row_elems,
+                                                  int metric, const float *qv, entry_t *c, int nc) {
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int lane = threadIdx.x & 31;
+    const int cpr = row_elems / EPC;
+    int ts = 1;
+    while (ts < cpr && ts < 32) ts <<= 1;
+    const int rpw = 32 / ts;
+    const int team = lane / ts, tl = lane & (ts - 1);
+    const int iters = (cpr + ts - 1) / ts;
+    const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
+    for (int c0 = 0; c0 < nc; c0 += rpw * U) {
+        float acc[U];
+        uint32_t id[U];
+        bool valid[U];
+        float sc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = c0 + u * rpw + team;
+            valid[u] = j < nc;
+            id[u] = valid[u] ? (uint32_t)(c[j] & 0xFFFFFFFFull) : 0u;
+            acc[u] = 0.f;
+            sc[u] = 1.f;
+            if (STORE == ANN_STORE_E4M3 && valid[u]) sc[u] = __ldg(scales + id[u]);
+        }
+        for (int it = 0; it < iters; ++it) {
+            const int ch = tl + it * ts;
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (valid[u] && ch < cpr) v[u] = ld_row_chunk(rbase + (size_t)id[u] * cpr + ch);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (valid[u] && ch < cpr) {
+                    const float *qc = qv + ch * EPC;
+                    acc[u] += metric == ANN_METRIC_L2 ? Chunk<STORE>::l2(v[u], qc, sc[u])
+                                                     : Chunk<STORE>::ip(v[u], qc, sc[u]);
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            for (int off = ts >> 1; off > 0; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
+            if (tl == 0 && valid[u]) {
+                const float key = metric == ANN_METRIC_L2 ? acc[u] : -acc[u];
+                c[c0 + u * rpw + team] = pack_entry(key, id[u]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Ascending sort of the 32 entries held one per lane.
+__device__ __forceinline__ entry_t warp_sort32(entry_t v) {
+    const int i = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) v = cmpx(v, j, k, i);
+    return v;
+}
+
+// Merge sorted, duplicate-free C[0..nc) into sorted Q[0..qlen) (all threads
+// of the block), keeping the first L entries in Qn. A candidate whose id is
+// already in Q is dropped; if it carries the checked flag the queued copy
+// takes it ("checked wins"). Adjacent equal candidates are also dropped.
+// dup is a byte buffer of >= nc entries, ctl_out an int in shared memory.
+// Returns the new length. Ends with a __syncthreads().
+template <int NT>
+__device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int L, entry_t *Qn,
+                                  unsigned char *dup, int *ctl_out, long long *dropped) {
+    int any = 0;
+    for (int j = threadIdx.x; j < nc; j += NT) {
+        const entry_t c = C[j] & kMask;
+        bool d = (j > 0 && (C[j - 1] & kMask) == c);
+        if (!d) {
+            const int pos = count_below(Q, qlen, c);
+            if (pos < qlen && (Q[pos] & kMask) == c) {
+                d = true;
+                if (C[j] & kChecked) Q[pos] |= kChecked;
+            }
+        }
+        dup[j] = d;
+        any |= d;
+    }
+    int ncl = nc;
+    if (__syncthreads_or(any)) {
+        if ((threadIdx.x >> 5) == 0) {
+            const int lane = threadIdx.x & 31;
+            int out = 0;
+            for (int b = 0; b < nc; b += 32) {
+                const int j = b + lane;
+                const bool keep = j < nc && !dup[j];
+                const entry_t c = j < nc ? C[j] : 0ull;
+                const unsigned bal = __ballot_sync(kFull, keep);
+                if (keep) C[out + __popc(bal & ((1u << lane) - 1u))] = c;
+                out += __popc(bal);
+            }
+            if (lane == 0) *ctl_out = out;
+        }
+        __syncthreads();
+        ncl = *ctl_out;
+        if (dropped) *dropped += nc - ncl;
+    }
+    for (int i = threadIdx.x; i < qlen; i += NT) {
+        const entry_t e = Q[i];
+        const int pos = i + count_below(C, ncl, e & kMask);
+        if (pos < L) Qn[pos] = e;
+    }
+    for (int j = threadIdx.x; j < ncl; j += NT) {
+        const entry_t c = C[j];
+        const int pos = j + count_below(Q, qlen, c & kMask);
+        if (pos < L) Qn[pos] = c;
+    }
+    __syncthreads();
+    return min(L, qlen + ncl);
+}
+
+}  // namespace ann

@@ -69,8 +69,9 @@ class Index:
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
                                  M_per_query=_ptr(M_per_query), stats=_ptr(stats))
 
-    def search(self, queries, k, L, M, *, out=None, stream=None, with_stats=False, **kw):
-        """queries: CUDA float32 nq x d. Returns (ids int64, dists float32[, stats int64 nq x 8])."""
+    def search(self, queries, k, L, M, *, out=None, stream=None, with_stats=False, stats=None, **kw):
+        """queries: CUDA float32 nq x d. Returns (ids int64, dists float32[, stats int64 nq x 8]).
+        ``stats`` may be a preallocated CUDA int64 nq x 8 tensor for the per-query counters."""
         q = queries.contiguous()
         if not q.is_cuda or q.dtype != torch.float32 or q.dim() != 2 or q.shape[1] != self.d:
             raise ValueError("queries must be a CUDA float32 tensor of shape nq x d")
@@ -80,7 +81,8 @@ class Index:
             dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
         else:
             ids, dists = out
-        stats = torch.empty((nq, 8), dtype=torch.int64, device=q.device) if with_stats else None
+        if stats is None and with_stats:
+            stats = torch.empty((nq, 8), dtype=torch.int64, device=q.device)
         p = self.params(stats=stats, **kw)
         _abi.ann_search_ex(self.handle, _ptr(q), nq, k, L, M, _ptr(ids), _ptr(dists), p,
                            _stream_handle(stream))

@@ -1,0 +1,92 @@
+"""GPU parity of the asynchronous walker kernel (Algorithm 3 + Algorithm 2).
+
+With a single walker (M = 1) everything in Algorithm 3 is sequential: the
+kernel must reproduce the oracle's lock-step simulation exactly, for every
+merge ratio R (deal, update positions, checker, merge). With several walkers
+the interleaving on the GPU is not deterministic by design (benign races on
+the shared visited map, Sec. 4.4); the kernel is then judged by recall@k
+against the exact ground truth, which must come within a tolerance of the
+oracle's simulated recall, and by the validity of every answer.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2201_13007_gb300 import synth  # noqa: E402
+from parity_util import compare_exact  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Index():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_13007_gb300.index import Index
+    return Index
+
+
+@pytest.fixture(scope="module")
+def sift():
+    return synth.make_workload("sift", 20000, 2000)
+
+
+def _search(Index, w, L, M, R, k=10, storage="f32", **kw):
+    ix = Index(w.base, w.adj, w.entry, storage=storage, metric=w.metric)
+    q = torch.from_numpy(w.queries).cuda()
+    ids, d, st = ix.search(q, k, L, M, mode="async", R_ratio=R, with_stats=True, **kw)
+    torch.cuda.synchronize()
+    out = ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy()
+    ix.close()
+    return out
+
+
+@pytest.mark.parametrize("R", [0.0, 0.5, 0.8, 1.0, float("inf")])
+@pytest.mark.parametrize("L", [16, 64, 150])
+def test_single_walker_is_exact(Index, oracle_mod, sift, R, L):
+    ids, d, st = _search(Index, sift, L, 1, R, hash_bits=15)
+    o_ids, o_keys, o_st = oracle_mod.search(sift.base, sift.adj, sift.entry, sift.queries, algo="speedann",
+                                            L=L, K=10, M0=1, M_max=1, R_ratio=R, nthreads=8)
+    compare_exact(ids, d, o_ids, o_keys)
+    np.testing.assert_array_equal(st[:, 2], o_st["evals"])        # distance evaluations
+    np.testing.assert_array_equal(st[:, 1], o_st["expansions"])
+    np.testing.assert_array_equal(st[:, 5], o_st["merges"])
+
+
+def _valid(ids, d, base, q):
+    for i in range(ids.shape[0]):
+        m = ids[i] >= 0
+        r = ids[i][m]
+        assert len(set(r.tolist())) == len(r), "duplicate id in a result"
+        k64 = ((base[r].astype(np.float64) - q[i].astype(np.float64)) ** 2).sum(1)
+        np.testing.assert_array_equal(d[i][m].astype(np.float64), k64)  # integer data: exact
+        order = np.lexsort((r, k64))
+        assert (order == np.arange(len(r))).all(), "result not in (key, id) order"
+
+
+@pytest.mark.parametrize("L,M,R", [(32, 2, 0.8), (64, 4, 0.8), (128, 8, 0.9), (64, 8, float("inf")),
+                                   (96, 16, 0.8), (64, 32, 0.9)])
+def test_multi_walker_recall_matches_oracle(Index, oracle_mod, sift, L, M, R):
+    ids, d, st = _search(Index, sift, L, M, R)
+    _valid(ids, d, sift.base, sift.queries)
+    gt, _ = oracle_mod.exact_knn(sift.base, sift.queries, 10, nthreads=8)
+    o_ids, _, o_st = oracle_mod.search(sift.base, sift.adj, sift.entry, sift.queries, algo="speedann", L=L,
+                                       K=10, M0=1, M_max=M, R_ratio=R, nthreads=8)
+    r_gpu = oracle_mod.recall(ids, gt).mean()
+    r_orc = oracle_mod.recall(o_ids, gt).mean()
+    # 2,000 queries x k=10: one id is worth 5e-5 of recall
+    assert abs(r_gpu - r_orc) <= 0.005, (r_gpu, r_orc)
+    assert (st[:, 5] >= 1).all()
+
+
+def test_async_rerank_and_storage(Index, sift):
+    w = sift
+    ix = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True)
+    q = torch.from_numpy(w.queries[:256]).cuda()
+    a = ix.search(q, 10, 64, 4, mode="async", R_ratio=0.8, rerank=True)
+    b = ix.search(q, 10, 64, 4, mode="async", R_ratio=0.8, rerank=True, persistent=True)
+    torch.cuda.synchronize()
+    for ids, d in (a, b):
+        _valid(ids.cpu().numpy(), d.cpu().numpy(), w.base, w.queries[:256])
+    ix.close()
