@@ -163,6 +163,35 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
                     int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
                     void *stream);
 
+/* Size of the static device array behind ann_search_host_noalloc. */
+#define ANN_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* ann_search_host for callers that cannot allocate device memory when they
+ * search: code running while a CUDA graph is captured on its thread (where
+ * cudaMalloc is not allowed), processes whose device memory is fully held by
+ * another framework's caching allocator, or latency-critical threads. The
+ * paper has no counterpart; this is a deployment convenience.
+ *   Arguments, layout and results are those of ann_search_host (host
+ *   buffers in and out, params may be NULL; the search always runs as a
+ *   persistent grid). The call allocates nothing: its device scratch (the
+ *   persistent grid's work counter and device copies of the queries and of
+ *   the results) lives in one static device array of
+ *   ANN_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the
+ *   library holds until the process exits.
+ *   A batch needing more than that (256 + nq*d*4 + nq*k*12 bytes, each part
+ *   rounded up to 256) is rejected with ANN_ERR_ARG and a message giving the
+ *   size and the limit.
+ *   The first call on a device resolves the array's address on that device
+ *   (this may load the module), so make that first call before any stream
+ *   capture.
+ *   All calls share the one array, which keeps the last call's contents;
+ *   calls that overlap on the GPU (other streams, other threads) race on it
+ *   and must be serialised by the caller. Synchronises the stream before it
+ *   returns. */
+int ann_search_host_noalloc(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
+                            int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
+                            void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ann_last_error(void);
 

@@ -19,6 +19,7 @@ METRIC = {"l2": 0, "ip": 1}
 MODE = {"sync": 0, "async": 1}
 ANN_INDEX_DEVICE_INPUT = 0x1
 ANN_INDEX_KEEP_F32 = 0x2
+ANN_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class AnnError(RuntimeError):
@@ -74,6 +75,8 @@ def lib():
             L.ann_search.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
             L.ann_search_ex.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
+            L.ann_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp,
+                                                  ctypes.POINTER(SearchParams), vp]
             L.ann_last_error.restype = ctypes.c_char_p
             L.ann_last_error.argtypes = []
             _lib = L
@@ -117,3 +120,8 @@ def ann_search_ex(index, queries, nq, k, L, M, out_ids, out_dists, params, strea
 def ann_search_host(index, queries, nq, k, L, M, out_ids, out_dists, params, stream) -> None:
     p = ctypes.byref(params) if params is not None else None
     _check(lib().ann_search_host(index, queries, nq, k, L, M, out_ids, out_dists, p, stream))
+
+
+def ann_search_host_noalloc(index, queries, nq, k, L, M, out_ids, out_dists, params, stream) -> None:
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().ann_search_host_noalloc(index, queries, nq, k, L, M, out_ids, out_dists, p, stream))

@@ -363,3 +363,99 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
 const char *ann_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free host-buffer search.
+//
+// For callers that must not allocate device memory at search time: code that
+// runs while a CUDA graph is being captured on its thread (cudaMalloc is not
+// allowed there), processes whose device memory is fully reserved by another
+// framework's caching allocator, or latency-critical threads that cannot
+// afford an allocator call. This entry point keeps all of its device scratch
+// (the persistent grid's work counter and the staging copies of the queries
+// and results) in one file-scope static device array, and calls no
+// cudaMalloc, cudaFree or other allocating routine.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)ANN_NOALLOC_SCRATCH_BYTES;
+
+// Every GPU that loads this library holds this array until the process
+// exits. In host code its name is only a stand-in for the symbol, never a
+// device address: the address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ANN_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256];  // device address of g_noalloc_scratch per device ordinal
+
+// Resolves the array's device address once per device, with that device
+// current. The first call on a device does this; it may load the module, so
+// that first call should happen before any stream capture.
+int noalloc_scratch_address(void **out) {
+    int dev = 0;
+    ANN_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(ANN_ERR_STATE, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ANN_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int ann_search_host_noalloc(const ann_index *index, const float *queries, int64_t nq, int32_t k,
+                                       int32_t L, int32_t M, int64_t *out_ids, float *out_dists,
+                                       const ann_search_params *params, void *stream) {
+    if (!index) return fail(ANN_ERR_ARG, "index is NULL");
+    if (nq == 0) return ANN_OK;
+    ann_search_params p;
+    memset(&p, 0, sizeof(p));
+    if (params) p = *params;
+    p.persistent = 1;
+    Plan plan;
+    int rc = plan_search(index, reinterpret_cast<const float *>(16), nq, k, L, M,
+                         reinterpret_cast<int64_t *>(16), reinterpret_cast<float *>(16), &p, &plan);
+    if (rc != ANN_OK) return rc;
+    if (!queries || !out_ids || !out_dists) return fail(ANN_ERR_ARG, "host pointers must not be NULL");
+    const ann::IndexData &x = index->d;
+    const size_t qb = (size_t)nq * x.d * 4, ib = (size_t)nq * k * 8, db = (size_t)nq * k * 4;
+    const size_t need = 256 + align256(qb) + align256(ib) + db;
+    if (need > kNoallocScratchBytes)
+        return fail(ANN_ERR_ARG,
+                    "batch needs %zu bytes of static device scratch (nq=%lld, d=%d, k=%d); the maximum is %zu bytes",
+                    need, (long long)nq, x.d, k, kNoallocScratchBytes);
+    int dev = 0;
+    ANN_CUDA(cudaGetDevice(&dev));
+    if (dev != x.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, x.device);
+    void *base = nullptr;
+    rc = noalloc_scratch_address(&base);
+    if (rc != ANN_OK) return rc;
+    char *sb = reinterpret_cast<char *>(base);
+    int *counter = reinterpret_cast<int *>(sb);
+    float *dq = reinterpret_cast<float *>(sb + 256);
+    int64_t *dids = reinterpret_cast<int64_t *>(sb + 256 + align256(qb));
+    float *ddist = reinterpret_cast<float *>(sb + 256 + align256(qb) + align256(ib));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    plan.a.queries = dq;
+    plan.a.out_ids = dids;
+    plan.a.out_dists = ddist;
+    plan.a.work_counter = counter;
+    plan.a.persistent = 1;
+    // the array keeps the previous call's contents: the counter must start at zero
+    ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    ANN_CUDA(cudaMemcpyAsync(dq, queries, qb, cudaMemcpyHostToDevice, s));
+    cudaError_t e = plan.mode == ANN_MODE_ASYNC
+                        ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
+                        : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "search launch");
+    ANN_CUDA(cudaMemcpyAsync(out_ids, dids, ib, cudaMemcpyDeviceToHost, s));
+    ANN_CUDA(cudaMemcpyAsync(out_dists, ddist, db, cudaMemcpyDeviceToHost, s));
+    ANN_CUDA(cudaStreamSynchronize(s));
+    return ANN_OK;
+}
