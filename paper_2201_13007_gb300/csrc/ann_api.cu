@@ -244,8 +244,28 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (a.rerank && L > need) need = L;
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
+    if (!async) {
+        // cp.async staging of gathered rows: auto = the rows of one full step,
+        // capped at 16 KB (at least one row; one FP32 row for the re-rank)
+        const int row_bytes = x.d_pad * ann::storage_bytes(x.storage);
+        const int row_bytes32 = x.d_pad32 * 4;
+        int sb = p->stage_bytes;
+        if (sb == 0) {
+            sb = M * x.R * (row_bytes + 4);
+            if (sb > 16384) sb = 16384;
+        }
+        if (sb > 0) {
+            if (sb < row_bytes + 4 || (a.rerank && sb < row_bytes32 + 4))
+                sb = (row_bytes > row_bytes32 ? row_bytes : row_bytes32) + 4;
+            a.stage_bytes = sb;
+            a.stage_rows = sb / (row_bytes + 4);
+            a.stage_rows32 = a.rerank ? sb / (row_bytes32 + 4) : 0;
+        } else if (sb != -1) {
+            return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
+        }
+    }
     int smem = async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, a.hash_bits)
-                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M).total;
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M, a.stage_bytes).total;
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
                     smem, max_dyn_smem());

@@ -405,3 +405,75 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
 }
 
 }  // namespace ann
+
+namespace ann {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// compute_keys with the rows staged through shared memory: the whole block
+// issues 16-byte cp.async copies of up to stage_rows candidate rows (and
+// their FP8 scales) at once, waits for them, then lane teams reduce each row
+// from shared memory. Many rows are in flight per CTA without holding them
+// in registers. stage holds stage_rows * row_bytes bytes (+ stage_rows
+// floats after it for the scales). Ends with a __syncthreads().
+template <int STORE, int NT>
+__device__ void compute_keys_staged(const void *rows, const float *scales, int row_elems, int metric,
+                                    const float *qv, entry_t *cand, int nc, unsigned char *stage,
+                                    int stage_rows) {
+    constexpr int NW = NT / 32;
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpr = row_elems / EPC;
+    const int row_bytes = cpr * 16;
+    int ts = 1;
+    while (ts < cpr && ts < 32) ts <<= 1;
+    const int rpw = 32 / ts;
+    const int team = lane / ts, tl = lane & (ts - 1);
+    const int iters = (cpr + ts - 1) / ts;
+    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
+    float *ssc = reinterpret_cast<float *>(stage + (size_t)stage_rows * row_bytes);
+    for (int b0 = 0; b0 < nc; b0 += stage_rows) {
+        const int nb = min(stage_rows, nc - b0);
+        for (int i = tid; i < nb * cpr; i += NT) {
+            const int r = i / cpr, ch = i - r * cpr;
+            const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
+            cp_async16(stage + (size_t)r * row_bytes + ch * 16, g + (size_t)id * row_bytes + ch * 16);
+        }
+        if (STORE == ANN_STORE_E4M3)
+            for (int r = tid; r < nb; r += NT) cp_async4(ssc + r, scales + (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull));
+        cp_async_wait_all();
+        __syncthreads();
+        for (int c0 = warp * rpw; c0 < nb; c0 += NW * rpw) {
+            const int r = c0 + team;
+            const bool valid = r < nb;
+            float acc = 0.f;
+            const float sc = (STORE == ANN_STORE_E4M3 && valid) ? ssc[r] : 1.f;
+            for (int it = 0; it < iters; ++it) {
+                const int ch = tl + it * ts;
+                if (valid && ch < cpr) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(stage + (size_t)r * row_bytes + ch * 16);
+                    const float *qc = qv + ch * EPC;
+                    acc += metric == ANN_METRIC_L2 ? Chunk<STORE>::l2(v, qc, sc) : Chunk<STORE>::ip(v, qc, sc);
+                }
+            }
+            for (int off = ts >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            if (tl == 0 && valid) {
+                const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
+                cand[b0 + r] = pack_entry(metric == ANN_METRIC_L2 ? acc : -acc, id);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ann

@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M);
+    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, a.stage_bytes);
+    unsigned char *stage = smem + lay.stage_off;
     float *qv = reinterpret_cast<float *>(smem + lay.q_off);
     entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
     entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
@@ -163,7 +164,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             evals += nc;
             if (nc > 0) {
                 // --- distances
-                compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc);
+                if (a.stage_rows > 0)
+                    compute_keys_staged<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, stage,
+                                                   a.stage_rows);
+                else
+                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc);
                 int P = 32;
                 while (P < nc) P <<= 1;
                 for (int i = nc + tid; i < P; i += NT) cand[i] = kEmptyEntry;
@@ -227,7 +232,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         if (a.rerank) {
             for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
             __syncthreads();
-            compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
+            if (a.stage_rows32 > 0)
+                compute_keys_staged<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen,
+                                                       stage, a.stage_rows32);
+            else
+                compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
             int P = 32;
             while (P < qlen) P <<= 1;
             for (int i = qlen + tid; i < P; i += NT) cand[i] = kEmptyEntry;
