@@ -102,8 +102,6 @@ typedef struct {
     int32_t threads;    /* threads per CTA: 0 = auto; sync 64..512; async 64..1024 and >= 32*M */
     int32_t hash_bits;  /* log2 slots of the per-query visited table; 0 = auto, else 8..15 */
     int32_t persistent; /* 1 = persistent grid that pulls queries from a device counter */
-    int32_t stage_bytes; /* sync mode: shared memory for cp.async staging of gathered rows;
-                          * 0 = auto, -1 = gather rows through registers, else >= one row */
     /* Per-query settings (device int32 arrays of nq entries, or NULL for the
      * uniform k, L, M arguments). When given, k, L and M passed to the call
      * are the maxima over the batch, and each entry must lie in [1, max]. */

@@ -48,7 +48,7 @@ class SearchParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("M0", ctypes.c_int32), ("t", ctypes.c_int32),
                 ("R_ratio", ctypes.c_float), ("rerank", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("hash_bits", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("stage_bytes", ctypes.c_int32), ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
+                ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
                 ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
 
 

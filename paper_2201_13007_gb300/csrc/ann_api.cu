@@ -174,7 +174,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
                 int64_t *out_ids, float *out_dists, const ann_search_params *p, Plan *plan) {
     if (!index) return fail(ANN_ERR_ARG, "index is NULL");
     const ann::IndexData &x = index->d;
-    if (nq < 0) return fail(ANN_ERR_ARG, "nq=%lld < 0", (long long)nq);
+    if (nq < 0 || nq > 0x7fffffffll) return fail(ANN_ERR_ARG, "nq=%lld outside [0, 2^31)", (long long)nq);
     if (nq > 0 && (!queries || !out_ids || !out_dists)) return fail(ANN_ERR_ARG, "queries/out pointers must not be NULL");
     if (L < 1 || L > 2048) return fail(ANN_ERR_ARG, "L=%d outside [1, 2048]", L);
     if (k < 1 || k > L) return fail(ANN_ERR_ARG, "k=%d outside [1, L=%d]", k, L);
@@ -244,28 +244,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (a.rerank && L > need) need = L;
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
-    if (!async) {
-        // cp.async staging of gathered rows: auto = the rows of one full step,
-        // capped at 16 KB (at least one row; one FP32 row for the re-rank)
-        const int row_bytes = x.d_pad * ann::storage_bytes(x.storage);
-        const int row_bytes32 = x.d_pad32 * 4;
-        int sb = p->stage_bytes;
-        if (sb == 0) {
-            sb = M * x.R * (row_bytes + 4);
-            if (sb > 16384) sb = 16384;
-        }
-        if (sb > 0) {
-            if (sb < row_bytes + 4 || (a.rerank && sb < row_bytes32 + 4))
-                sb = (row_bytes > row_bytes32 ? row_bytes : row_bytes32) + 4;
-            a.stage_bytes = sb;
-            a.stage_rows = sb / (row_bytes + 4);
-            a.stage_rows32 = a.rerank ? sb / (row_bytes32 + 4) : 0;
-        } else if (sb != -1) {
-            return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
-        }
-    }
     int smem = async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, a.hash_bits)
-                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M, a.stage_bytes).total;
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M).total;
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
                     smem, max_dyn_smem());

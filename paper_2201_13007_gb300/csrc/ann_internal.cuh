@@ -64,30 +64,26 @@ struct SearchArgs {
     int32_t Lcap;        // queue capacity
     int32_t Ccap;        // candidate / sort buffer, power of two >= 32
     int32_t qfloats;     // query buffer length
-    int32_t stage_bytes; // cp.async staging area (0 = gather rows through registers)
-    int32_t stage_rows;  // stored rows per staging batch
-    int32_t stage_rows32;// FP32 re-rank rows per staging batch
 };
 
 // Byte offsets of the dynamic shared-memory segments (16-byte aligned).
 struct SmemLayout {
-    int q_off, q0_off, q1_off, cand_off, dup_off, hash_off, act_off, stage_off, total;
+    int q_off, q0_off, q1_off, cand_off, cand2_off, dup_off, hash_off, act_off, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
-                                                  int stage_bytes) {
+__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap) {
     SmemLayout s;
     int o = 0;
     s.q_off = o;    o += align16(qfloats * 4);
     s.q0_off = o;   o += align16(Lcap * 8);
     s.q1_off = o;   o += align16(Lcap * 8);
     s.cand_off = o; o += align16(Ccap * 8);
+    s.cand2_off = o; o += align16(Ccap * 8);
     s.dup_off = o;  o += align16(Ccap);
     s.hash_off = o; o += align16((1 << hash_bits) * 4);
     s.act_off = o;  o += align16(Mcap * 4);
-    s.stage_off = o; o += align16(stage_bytes);
     s.total = o;
     return s;
 }

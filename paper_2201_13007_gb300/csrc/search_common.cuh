@@ -30,33 +30,57 @@ __device__ __forceinline__ uint32_t entry_id(entry_t e) { return (uint32_t)(e & 
 __device__ __forceinline__ float entry_key(entry_t e) { return key_value((uint32_t)(e >> 32)); }
 
 // -------------------------------------------------------- distance gather
+// Packed two-lane FP32 arithmetic (sub.f32x2 / fma.f32x2 / mul.f32x2): each
+// instruction does the work of two scalar ones, each lane rounded exactly as
+// the scalar operation would be.
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long u) {
+    return make_float2(__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32)));
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+// acc += (q - x)^2 (L2) or acc += q * x (inner product), two lanes at a time
+__device__ __forceinline__ void acc_pair(float2 &acc, float2 q, float2 x, bool l2) {
+    if (l2) {
+        const float2 d = sub2(q, x);
+        acc = fma2(d, d, acc);
+    } else {
+        acc = fma2(q, x, acc);
+    }
+}
+
 // One 16-byte chunk of a stored row against the matching FP32 query
-// elements. L2: sum (q - x)^2; IP: sum q * x (negated by the caller).
+// elements, accumulated into a packed pair of partial sums.
 template <int STORE> struct Chunk;
 
 template <> struct Chunk<ANN_STORE_F32> {
     static constexpr int kElems = 4;
-    __device__ static __forceinline__ float l2(const uint4 c, const float *q, float) {
-        float acc = 0.f, t;
-        t = q[0] - __uint_as_float(c.x); acc = fmaf(t, t, acc);
-        t = q[1] - __uint_as_float(c.y); acc = fmaf(t, t, acc);
-        t = q[2] - __uint_as_float(c.z); acc = fmaf(t, t, acc);
-        t = q[3] - __uint_as_float(c.w); acc = fmaf(t, t, acc);
-        return acc;
-    }
-    __device__ static __forceinline__ float ip(const uint4 c, const float *q, float) {
-        float acc = q[0] * __uint_as_float(c.x);
-        acc = fmaf(q[1], __uint_as_float(c.y), acc);
-        acc = fmaf(q[2], __uint_as_float(c.z), acc);
-        acc = fmaf(q[3], __uint_as_float(c.w), acc);
-        return acc;
+    __device__ static __forceinline__ void add(float2 &acc, const uint4 c, const float *q, float, bool l2) {
+        const float4 qq = *reinterpret_cast<const float4 *>(q);
+        acc_pair(acc, make_float2(qq.x, qq.y), make_float2(__uint_as_float(c.x), __uint_as_float(c.y)), l2);
+        acc_pair(acc, make_float2(qq.z, qq.w), make_float2(__uint_as_float(c.z), __uint_as_float(c.w)), l2);
     }
 };
 
 template <typename H2> __device__ __forceinline__ float2 to_f2(uint32_t w);
 template <> __device__ __forceinline__ float2 to_f2<__nv_bfloat162>(uint32_t w) {
-    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&w);
-    return __bfloat1622float2(h);
+    // bfloat16 -> float is exact: the 16 bits become the high half of the float
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
 }
 template <> __device__ __forceinline__ float2 to_f2<__half2>(uint32_t w) {
     __half2 h = *reinterpret_cast<__half2 *>(&w);
@@ -65,28 +89,13 @@ template <> __device__ __forceinline__ float2 to_f2<__half2>(uint32_t w) {
 
 template <typename H2> struct Chunk16 {
     static constexpr int kElems = 8;
-    __device__ static __forceinline__ float l2(const uint4 c, const float *q, float) {
-        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
-        float acc = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float2 v = to_f2<H2>(w[i]);
-            float t0 = q[2 * i] - v.x, t1 = q[2 * i + 1] - v.y;
-            acc = fmaf(t0, t0, acc);
-            acc = fmaf(t1, t1, acc);
-        }
-        return acc;
-    }
-    __device__ static __forceinline__ float ip(const uint4 c, const float *q, float) {
-        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
-        float acc = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float2 v = to_f2<H2>(w[i]);
-            acc = fmaf(q[2 * i], v.x, acc);
-            acc = fmaf(q[2 * i + 1], v.y, acc);
-        }
-        return acc;
+    __device__ static __forceinline__ void add(float2 &acc, const uint4 c, const float *q, float, bool l2) {
+        const float4 qa = *reinterpret_cast<const float4 *>(q);
+        const float4 qb = *reinterpret_cast<const float4 *>(q + 4);
+        acc_pair(acc, make_float2(qa.x, qa.y), to_f2<H2>(c.x), l2);
+        acc_pair(acc, make_float2(qa.z, qa.w), to_f2<H2>(c.y), l2);
+        acc_pair(acc, make_float2(qb.x, qb.y), to_f2<H2>(c.z), l2);
+        acc_pair(acc, make_float2(qb.z, qb.w), to_f2<H2>(c.w), l2);
     }
 };
 template <> struct Chunk<ANN_STORE_BF16> : Chunk16<__nv_bfloat162> {};
@@ -96,35 +105,17 @@ template <> struct Chunk<ANN_STORE_E4M3> {
     static constexpr int kElems = 16;
     __device__ static __forceinline__ float2 dq(uint16_t pair, float s) {
         __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
-        float2 f = __half22float2(*reinterpret_cast<__half2 *>(&hr));
-        return make_float2(__fmul_rn(s, f.x), __fmul_rn(s, f.y));
+        const float2 f = __half22float2(*reinterpret_cast<__half2 *>(&hr));
+        return mul2(make_float2(s, s), f);  // the stored value: float32(scale * code)
     }
-    __device__ static __forceinline__ float l2(const uint4 c, const float *q, float s) {
+    __device__ static __forceinline__ void add(float2 &acc, const uint4 c, const float *q, float s, bool l2) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
-        float acc = 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            float2 a = dq((uint16_t)(w[i] & 0xFFFF), s), b = dq((uint16_t)(w[i] >> 16), s);
-            float t;
-            t = q[4 * i] - a.x;     acc = fmaf(t, t, acc);
-            t = q[4 * i + 1] - a.y; acc = fmaf(t, t, acc);
-            t = q[4 * i + 2] - b.x; acc = fmaf(t, t, acc);
-            t = q[4 * i + 3] - b.y; acc = fmaf(t, t, acc);
+            const float4 qq = *reinterpret_cast<const float4 *>(q + 4 * i);
+            acc_pair(acc, make_float2(qq.x, qq.y), dq((uint16_t)(w[i] & 0xFFFF), s), l2);
+            acc_pair(acc, make_float2(qq.z, qq.w), dq((uint16_t)(w[i] >> 16), s), l2);
         }
-        return acc;
-    }
-    __device__ static __forceinline__ float ip(const uint4 c, const float *q, float s) {
-        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
-        float acc = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float2 a = dq((uint16_t)(w[i] & 0xFFFF), s), b = dq((uint16_t)(w[i] >> 16), s);
-            acc = fmaf(q[4 * i], a.x, acc);
-            acc = fmaf(q[4 * i + 1], a.y, acc);
-            acc = fmaf(q[4 * i + 2], b.x, acc);
-            acc = fmaf(q[4 * i + 3], b.y, acc);
-        }
-        return acc;
     }
 };
 
@@ -136,14 +127,18 @@ __device__ __forceinline__ uint4 ld_row_chunk(const uint4 *p) {
     return v;
 }
 
-// Keys of the nc candidates whose ids sit in the low word of cand[0..nc),
-// written back packed. A team of TS lanes (a power of two, TS >= chunks per
-// row when the row has at most 32 chunks) gathers one row with 16-byte
-// loads; each team keeps U rows in flight; partial sums are reduced with
-// xor shuffles inside the team. All warps of the block take part.
+// Keys of the nc candidates whose ids sit in the low word of cand[0..nc).
+// A team of TS lanes (a power of two, TS >= chunks per row when the row has
+// at most 32 chunks) gathers one row with 16-byte loads; each team keeps U
+// rows in flight; partial sums are reduced with xor shuffles inside the team.
+// All warps of the block take part. With out == nullptr the packed entries
+// are written back in place; otherwise only entries below `limit` (in
+// (key, id) order) are appended to out[] through the shared counter *out_n.
 template <int STORE, int NT, int U = 2>
 __device__ __forceinline__ void compute_keys(const void *rows, const float *scales, int row_elems,
-                                             int metric, const float *qv, entry_t *cand, int nc) {
+                                             int metric, const float *qv, entry_t *cand, int nc,
+                                             entry_t limit = kEmptyEntry, entry_t *out = nullptr,
+                                             int *out_n = nullptr) {
     constexpr int NW = NT / 32;
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -153,18 +148,19 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
     const int rpw = 32 / ts;
     const int team = lane / ts, tl = lane & (ts - 1);
     const int iters = (cpr + ts - 1) / ts;
+    const bool l2 = metric == ANN_METRIC_L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
     for (int c0 = warp * rpw * U; c0 < nc; c0 += NW * rpw * U) {
-        float acc[U];
+        float2 acc[U];
         uint32_t id[U];
         bool valid[U];
         float sc[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            int c = c0 + u * rpw + team;
+            const int c = c0 + u * rpw + team;
             valid[u] = c < nc;
             id[u] = valid[u] ? (uint32_t)(cand[c] & 0xFFFFFFFFull) : 0u;
-            acc[u] = 0.f;
+            acc[u] = make_float2(0.f, 0.f);
             sc[u] = 1.f;
             if (STORE == ANN_STORE_E4M3 && valid[u]) sc[u] = __ldg(scales + id[u]);
         }
@@ -176,18 +172,23 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
                 if (valid[u] && ch < cpr) v[u] = ld_row_chunk(rbase + (size_t)id[u] * cpr + ch);
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (valid[u] && ch < cpr) {
-                    const float *qc = qv + ch * EPC;
-                    acc[u] += metric == ANN_METRIC_L2 ? Chunk<STORE>::l2(v[u], qc, sc[u])
-                                                     : Chunk<STORE>::ip(v[u], qc, sc[u]);
-                }
+                if (valid[u] && ch < cpr) Chunk<STORE>::add(acc[u], v[u], qv + ch * EPC, sc[u], l2);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            for (int off = ts >> 1; off > 0; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
-            if (tl == 0 && valid[u]) {
-                float key = metric == ANN_METRIC_L2 ? acc[u] : -acc[u];
-                cand[c0 + u * rpw + team] = pack_entry(key, id[u]);
+            float r = acc[u].x + acc[u].y;
+            for (int off = ts >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+            const entry_t e = pack_entry(l2 ? r : -r, id[u]);
+            const bool write = tl == 0 && valid[u];
+            if (out == nullptr) {
+                if (write) cand[c0 + u * rpw + team] = e;
+            } else {
+                const bool keep = write && e < limit;
+                const unsigned bal = __ballot_sync(kFull, keep);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
             }
         }
     }
@@ -297,9 +298,10 @@ __device__ __forceinline__ void warp_compute_keys(const void *rows, const float 
     const int rpw = 32 / ts;
     const int team = lane / ts, tl = lane & (ts - 1);
     const int iters = (cpr + ts - 1) / ts;
+    const bool l2 = metric == ANN_METRIC_L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
     for (int c0 = 0; c0 < nc; c0 += rpw * U) {
-        float acc[U];
+        float2 acc[U];
         uint32_t id[U];
         bool valid[U];
         float sc[U];
@@ -308,7 +310,7 @@ __device__ __forceinline__ void warp_compute_keys(const void *rows, const float 
             const int j = c0 + u * rpw + team;
             valid[u] = j < nc;
             id[u] = valid[u] ? (uint32_t)(c[j] & 0xFFFFFFFFull) : 0u;
-            acc[u] = 0.f;
+            acc[u] = make_float2(0.f, 0.f);
             sc[u] = 1.f;
             if (STORE == ANN_STORE_E4M3 && valid[u]) sc[u] = __ldg(scales + id[u]);
         }
@@ -320,19 +322,13 @@ __device__ __forceinline__ void warp_compute_keys(const void *rows, const float 
                 if (valid[u] && ch < cpr) v[u] = ld_row_chunk(rbase + (size_t)id[u] * cpr + ch);
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (valid[u] && ch < cpr) {
-                    const float *qc = qv + ch * EPC;
-                    acc[u] += metric == ANN_METRIC_L2 ? Chunk<STORE>::l2(v[u], qc, sc[u])
-                                                     : Chunk<STORE>::ip(v[u], qc, sc[u]);
-                }
+                if (valid[u] && ch < cpr) Chunk<STORE>::add(acc[u], v[u], qv + ch * EPC, sc[u], l2);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            for (int off = ts >> 1; off > 0; off >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], off);
-            if (tl == 0 && valid[u]) {
-                const float key = metric == ANN_METRIC_L2 ? acc[u] : -acc[u];
-                c[c0 + u * rpw + team] = pack_entry(key, id[u]);
-            }
+            float r = acc[u].x + acc[u].y;
+            for (int off = ts >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+            if (tl == 0 && valid[u]) c[c0 + u * rpw + team] = pack_entry(l2 ? r : -r, id[u]);
         }
     }
     __syncwarp();
@@ -407,73 +403,5 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
 }  // namespace ann
 
 namespace ann {
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-// compute_keys with the rows staged through shared memory: the whole block
-// issues 16-byte cp.async copies of up to stage_rows candidate rows (and
-// their FP8 scales) at once, waits for them, then lane teams reduce each row
-// from shared memory. Many rows are in flight per CTA without holding them
-// in registers. stage holds stage_rows * row_bytes bytes (+ stage_rows
-// floats after it for the scales). Ends with a __syncthreads().
-template <int STORE, int NT>
-__device__ void compute_keys_staged(const void *rows, const float *scales, int row_elems, int metric,
-                                    const float *qv, entry_t *cand, int nc, unsigned char *stage,
-                                    int stage_rows) {
-    constexpr int NW = NT / 32;
-    constexpr int EPC = Chunk<STORE>::kElems;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cpr = row_elems / EPC;
-    const int row_bytes = cpr * 16;
-    int ts = 1;
-    while (ts < cpr && ts < 32) ts <<= 1;
-    const int rpw = 32 / ts;
-    const int team = lane / ts, tl = lane & (ts - 1);
-    const int iters = (cpr + ts - 1) / ts;
-    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
-    float *ssc = reinterpret_cast<float *>(stage + (size_t)stage_rows * row_bytes);
-    for (int b0 = 0; b0 < nc; b0 += stage_rows) {
-        const int nb = min(stage_rows, nc - b0);
-        for (int i = tid; i < nb * cpr; i += NT) {
-            const int r = i / cpr, ch = i - r * cpr;
-            const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
-            cp_async16(stage + (size_t)r * row_bytes + ch * 16, g + (size_t)id * row_bytes + ch * 16);
-        }
-        if (STORE == ANN_STORE_E4M3)
-            for (int r = tid; r < nb; r += NT) cp_async4(ssc + r, scales + (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull));
-        cp_async_wait_all();
-        __syncthreads();
-        for (int c0 = warp * rpw; c0 < nb; c0 += NW * rpw) {
-            const int r = c0 + team;
-            const bool valid = r < nb;
-            float acc = 0.f;
-            const float sc = (STORE == ANN_STORE_E4M3 && valid) ? ssc[r] : 1.f;
-            for (int it = 0; it < iters; ++it) {
-                const int ch = tl + it * ts;
-                if (valid && ch < cpr) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(stage + (size_t)r * row_bytes + ch * 16);
-                    const float *qc = qv + ch * EPC;
-                    acc += metric == ANN_METRIC_L2 ? Chunk<STORE>::l2(v, qc, sc) : Chunk<STORE>::ip(v, qc, sc);
-                }
-            }
-            for (int off = ts >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-            if (tl == 0 && valid) {
-                const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
-                cand[b0 + r] = pack_entry(metric == ANN_METRIC_L2 ? acc : -acc, id);
-            }
-        }
-        __syncthreads();
-    }
-}
 
 }  // namespace ann

@@ -34,7 +34,11 @@ struct Ctrl {
     int qlen;
     int hash_count;
     int anydup;
-    long long qi;
+    int ns;      // candidates that beat the L-th queued entry this step
+    int unsafe;  // 1 once the visited table may have forgotten a vertex this query
+    int qi;
+    // per-query counters, updated by thread 0 only
+    long long steps, expansions, evals, resets, dropped, t0;
 };
 
 template <int NT, int STORE>
@@ -42,12 +46,12 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, a.stage_bytes);
-    unsigned char *stage = smem + lay.stage_off;
+    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M);
     float *qv = reinterpret_cast<float *>(smem + lay.q_off);
     entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
     entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
     entry_t *cand = reinterpret_cast<entry_t *>(smem + lay.cand_off);
+    entry_t *surv = reinterpret_cast<entry_t *>(smem + lay.cand2_off);
     unsigned char *dup = smem + lay.dup_off;
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
     int *act = reinterpret_cast<int *>(smem + lay.act_off);
@@ -56,24 +60,24 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
 
     for (;;) {
         if (tid == 0) {
-            long long qi = a.persistent ? (long long)atomicAdd(a.work_counter, 1) : (long long)blockIdx.x;
-            ctl.qi = qi;
+            ctl.qi = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
+            ctl.t0 = global_ns();
+            ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
+            ctl.evals = 1;
+            ctl.unsafe = 0;
         }
         __syncthreads();
-        const long long qi = ctl.qi;
+        const int qi = ctl.qi;
         if (qi >= a.nq) break;
-        const int64_t t0 = global_ns();
 
         const int k = a.k_arr ? a.k_arr[qi] : a.k;
         const int L = a.L_arr ? a.L_arr[qi] : a.L;
         const int Mmax = a.M_arr ? a.M_arr[qi] : a.M;
-        int64_t *oid = a.out_ids + (size_t)qi * a.k;
-        float *odist = a.out_dists + (size_t)qi * a.k;
         const bool bad = k < 1 || k > a.k || L < k || L > a.L || Mmax < 1 || Mmax > a.M;
         if (bad) {
             for (int i = tid; i < a.k; i += NT) {
-                oid[i] = -1;
-                odist[i] = __int_as_float(0x7f800000);
+                a.out_ids[(size_t)qi * a.k + i] = -1;
+                a.out_dists[(size_t)qi * a.k + i] = __int_as_float(0x7f800000);
             }
             if (tid == 0 && a.stats) {
                 ann_query_stats st = {};
@@ -102,8 +106,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         }
         __syncthreads();
 
-        long long steps = 0, expansions = 0, evals = 1, resets = 0, dropped = 0;
         int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
+        int step = 0;
         entry_t *Q = Qa, *Qn = Qb;
         for (;;) {
             int qlen = ctl.qlen;
@@ -112,8 +116,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
                 __syncthreads();
                 for (int i = tid; i < qlen; i += NT) visited_insert(table, a.hash_bits, entry_id(Q[i]));
-                if (tid == 0) ctl.hash_count = qlen;
-                resets++;
+                if (tid == 0) {
+                    ctl.hash_count = qlen;
+                    ctl.resets++;
+                    ctl.unsafe = 1;
+                }
             }
             // --- select the first Mcur unchecked entries (rank order) and mark them
             if (warp == 0) {
@@ -134,13 +141,17 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     ctl.nact = found < Mcur ? found : Mcur;
                     ctl.ncand = 0;
                     ctl.anydup = 0;
+                    ctl.ns = 0;
                 }
             }
             __syncthreads();
             const int nact = ctl.nact;
             if (nact == 0) break;  // no unchecked vertex left
-            steps++;
-            expansions += nact;
+            step++;
+            if (tid == 0) {
+                ctl.steps++;
+                ctl.expansions += nact;
+            }
 
             // --- expand: adjacency rows -> visited filter -> candidate ids
             const int total = nact * R;
@@ -151,7 +162,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     const int aidx = i / R, r = i - aidx * R;
                     u = __ldg(a.adj + (size_t)act[aidx] * R + r);
                 }
-                const bool fresh = u >= 0 && visited_insert(table, a.hash_bits, (uint32_t)u) != 0;
+                const int ins = u >= 0 ? visited_insert(table, a.hash_bits, (uint32_t)u) : 0;
+                if (ins == 2) ctl.unsafe = 1;  // probe limit hit: this vertex may be a repeat
+                const bool fresh = ins != 0;
                 const unsigned bal = __ballot_sync(kFull, fresh);
                 int basepos = 0;
                 if (lane == 0 && bal) basepos = atomicAdd(&ctl.ncand, __popc(bal));
@@ -160,70 +173,84 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             }
             __syncthreads();
             const int nc = ctl.ncand;
-            if (tid == 0) ctl.hash_count += nc;
-            evals += nc;
+            if (tid == 0) {
+                ctl.hash_count += nc;
+                ctl.evals += nc;
+            }
             if (nc > 0) {
-                // --- distances
-                if (a.stage_rows > 0)
-                    compute_keys_staged<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, stage,
-                                                   a.stage_rows);
-                else
-                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc);
-                int P = 32;
-                while (P < nc) P <<= 1;
-                for (int i = nc + tid; i < P; i += NT) cand[i] = kEmptyEntry;
+                // --- distances; only candidates below the L-th queued entry survive
+                const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
+                compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
                 __syncthreads();
-                // --- sort the candidates by (key, id)
-                block_bitonic_sort<NT>(cand, P);
-                // --- drop ids already queued or repeated in this step
-                int any = 0;
-                for (int j = tid; j < nc; j += NT) {
-                    const entry_t c = cand[j];
-                    bool d = (j > 0 && cand[j - 1] == c);
-                    if (!d) {
-                        const int pos = count_below(Q, qlen, c);
-                        d = pos < qlen && (Q[pos] & kMask) == c;
-                    }
-                    dup[j] = d;
-                    any |= d;
-                }
-                int ncl = nc;
-                if (__syncthreads_or(any)) {
-                    if (warp == 0) {
-                        int out = 0;
-                        for (int b = 0; b < nc; b += 32) {
-                            const int j = b + lane;
-                            const bool keep = j < nc && !dup[j];
-                            const entry_t c = j < nc ? cand[j] : 0ull;
-                            const unsigned bal = __ballot_sync(kFull, keep);
-                            if (keep) cand[out + __popc(bal & ((1u << lane) - 1u))] = c;
-                            out += __popc(bal);
+                const int ns = ctl.ns;
+                if (ns > 0) {
+                    // --- sort the survivors by (key, id)
+                    if (ns <= 32) {
+                        if (warp == 0) {
+                            entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
+                            e = warp_sort32(e);
+                            surv[lane] = e;
                         }
-                        if (lane == 0) ctl.anydup = out;
+                        __syncthreads();
+                    } else {
+                        int P = 64;
+                        while (P < ns) P <<= 1;
+                        for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+                        __syncthreads();
+                        block_bitonic_sort<NT>(surv, P);
+                    }
+                    int ncl = ns;
+                    if (ctl.unsafe) {
+                        // --- drop ids already queued or repeated (only after the table forgot)
+                        int any = 0;
+                        for (int j = tid; j < ns; j += NT) {
+                            const entry_t c = surv[j];
+                            bool d = (j > 0 && surv[j - 1] == c);
+                            if (!d) {
+                                const int pos = count_below(Q, qlen, c);
+                                d = pos < qlen && (Q[pos] & kMask) == c;
+                            }
+                            dup[j] = d;
+                            any |= d;
+                        }
+                        if (__syncthreads_or(any)) {
+                            if (warp == 0) {
+                                int outp = 0;
+                                for (int b = 0; b < ns; b += 32) {
+                                    const int j = b + lane;
+                                    const bool keep = j < ns && !dup[j];
+                                    const entry_t c = j < ns ? surv[j] : 0ull;
+                                    const unsigned bal = __ballot_sync(kFull, keep);
+                                    if (keep) surv[outp + __popc(bal & ((1u << lane) - 1u))] = c;
+                                    outp += __popc(bal);
+                                }
+                                if (lane == 0) ctl.anydup = outp;
+                            }
+                            __syncthreads();
+                            ncl = ctl.anydup;
+                            if (tid == 0) ctl.dropped += ns - ncl;
+                        }
+                    }
+                    // --- merge queue and survivors by rank, truncate to L
+                    for (int i = tid; i < qlen; i += NT) {
+                        const entry_t e = Q[i];
+                        const int pos = i + count_below(surv, ncl, e & kMask);
+                        if (pos < L) Qn[pos] = e;
+                    }
+                    for (int j = tid; j < ncl; j += NT) {
+                        const entry_t c = surv[j];
+                        const int pos = j + count_below(Q, qlen, c);
+                        if (pos < L) Qn[pos] = c;
                     }
                     __syncthreads();
-                    ncl = ctl.anydup;
-                    dropped += nc - ncl;
+                    if (tid == 0) ctl.qlen = min(L, qlen + ncl);
+                    entry_t *tmp = Q;
+                    Q = Qn;
+                    Qn = tmp;
                 }
-                // --- merge queue and candidates by rank, truncate to L
-                for (int i = tid; i < qlen; i += NT) {
-                    const entry_t e = Q[i];
-                    const int pos = i + count_below(cand, ncl, e & kMask);
-                    if (pos < L) Qn[pos] = e;
-                }
-                for (int j = tid; j < ncl; j += NT) {
-                    const entry_t c = cand[j];
-                    const int pos = j + count_below(Q, qlen, c);
-                    if (pos < L) Qn[pos] = c;
-                }
-                __syncthreads();
-                if (tid == 0) ctl.qlen = min(L, qlen + ncl);
-                entry_t *tmp = Q;
-                Q = Qn;
-                Qn = tmp;
             }
             __syncthreads();
-            if (steps % a.t == 0) Mcur = min(2 * Mcur, Mmax);
+            if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
         }
 
         // --- output: first k of the queue, optionally re-ranked with FP32 rows
@@ -232,11 +259,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         if (a.rerank) {
             for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
             __syncthreads();
-            if (a.stage_rows32 > 0)
-                compute_keys_staged<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen,
-                                                       stage, a.stage_rows32);
-            else
-                compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
+            compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
             int P = 32;
             while (P < qlen) P <<= 1;
             for (int i = qlen + tid; i < P; i += NT) cand[i] = kEmptyEntry;
@@ -244,8 +267,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             block_bitonic_sort<NT>(cand, P);
             res = cand;
         }
-        for (int i = tid; i < k; i += NT) {
-            if (i < qlen) {
+        int64_t *oid = a.out_ids + (size_t)qi * a.k;
+        float *odist = a.out_dists + (size_t)qi * a.k;
+        for (int i = tid; i < a.k; i += NT) {
+            if (i < k && i < qlen) {
                 oid[i] = (int64_t)entry_id(res[i]);
                 odist[i] = entry_key(res[i]);
             } else {
@@ -253,19 +278,15 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 odist[i] = __int_as_float(0x7f800000);
             }
         }
-        for (int i = k + tid; i < a.k; i += NT) {
-            oid[i] = -1;
-            odist[i] = __int_as_float(0x7f800000);
-        }
         if (tid == 0 && a.stats) {
             ann_query_stats st;
-            st.steps = steps;
-            st.expansions = expansions;
-            st.evals = evals;
-            st.hash_resets = resets;
-            st.dup_dropped = dropped;
+            st.steps = ctl.steps;
+            st.expansions = ctl.expansions;
+            st.evals = ctl.evals;
+            st.hash_resets = ctl.resets;
+            st.dup_dropped = ctl.dropped;
             st.merges = 0;
-            st.t_start_ns = t0;
+            st.t_start_ns = ctl.t0;
             st.t_end_ns = global_ns();
             a.stats[qi] = st;
         }

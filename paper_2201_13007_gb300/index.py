@@ -63,11 +63,9 @@ class Index:
 
     @staticmethod
     def params(mode="sync", M0=1, t=1, R_ratio=0.8, rerank=False, threads=0, hash_bits=0,
-               persistent=False, stage_bytes=0, k_per_query=None, L_per_query=None, M_per_query=None,
-               stats=None):
+               persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None):
         return _abi.SearchParams(mode=_abi.MODE[mode], M0=M0, t=t, R_ratio=R_ratio, rerank=int(rerank),
                                  threads=threads, hash_bits=hash_bits, persistent=int(persistent),
-                                 stage_bytes=stage_bytes,
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
                                  M_per_query=_ptr(M_per_query), stats=_ptr(stats))
 
