@@ -36,8 +36,9 @@ sys.path.insert(0, ROOT)
 
 K = 10
 TARGETS = (0.9, 0.99)
-L_SWEEP = (10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512)
-M_SWEEP = (1, 2, 4, 8, 16)
+L_SWEEP = (10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024,
+           1280, 1536, 2048)
+M_SWEEP = (4, 8, 16, 32)
 
 
 def parse():

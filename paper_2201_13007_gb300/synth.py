@@ -18,7 +18,8 @@ Workload recipes (n x d, components, distribution):
   excluded) + reverse edges by ascending distance, degree cap 24.
 - ``sift``   n x 128 integer-valued (0..255) vectors: 64 components, means
   U[0,255]^128 * 0.5 + 64, sigma 60, rounded to nearest and clipped to
-  [0, 255]; graph = 64-NN, occlusion prune to 32, reverse fill to 32. (With
+  [0, 255]; graph = occlusion prune to 32 of the union of each vertex's 64-NN
+  and reverse 64-NN lists (first 128 by distance), then reverse fill to 32. (With
   sigma 30 the components are disjoint islands and no pruned k-NN graph over
   them is navigable: recall@10 stays below 0.75 at L = 256.)
 - ``gist``   n x 960 non-negative: 32 components, x = exp(mu_c + 0.5 z),
@@ -355,10 +356,54 @@ def build_knn_reverse_graph(x, k=16, cap=24):
     return reverse_fill(x, ids, cap), ids
 
 
-def build_pruned_graph(x, R=32, k=64):
-    """k-NN candidates, occlusion prune to R, reverse fill to R."""
+def union_candidates(ids: np.ndarray, dd: np.ndarray, cap: int):
+    """Per vertex, the union of its k-NN list and of the vertices that list it
+    (reverse k-NN), deduplicated, sorted by (distance, id) and cut to ``cap``.
+    Returns (ids int32 n x cap, squared distances float32 n x cap; padding
+    has distance +inf). Runs on the torch device."""
+    import torch
+    dev = _torch_device()
+    n, k = ids.shape
+    I = torch.from_numpy(ids.astype(np.int64)).to(dev)
+    W = torch.from_numpy(dd.astype(np.float32)).to(dev)
+    own = torch.arange(n, device=dev).repeat_interleave(k)
+    c = I.reshape(-1)
+    w = W.reshape(-1)
+    o2 = torch.cat([own, c])
+    c2 = torch.cat([c, own])
+    w2 = torch.cat([w, w])
+    del I, W, own, c, w
+    # dedupe (owner, candidate) pairs
+    key = o2 * n + c2
+    key, order = torch.sort(key)
+    w2 = w2[order]
+    keep = torch.ones_like(key, dtype=torch.bool)
+    keep[1:] = key[1:] != key[:-1]
+    key, w2 = key[keep], w2[keep]
+    o2 = key // n
+    c2 = key % n
+    # sort by (owner, distance, candidate): stable sorts from the last key to the first
+    order = torch.argsort(w2, stable=True)          # (ties keep ascending candidate order from above)
+    o2, c2, w2 = o2[order], c2[order], w2[order]
+    order = torch.argsort(o2, stable=True)
+    o2, c2, w2 = o2[order], c2[order], w2[order]
+    counts = torch.bincount(o2, minlength=n)
+    first = torch.cumsum(counts, 0) - counts
+    rank = torch.arange(o2.shape[0], device=dev) - first[o2]
+    m = rank < cap
+    cand = torch.zeros((n, cap), dtype=torch.int32, device=dev)
+    cdist = torch.full((n, cap), float("inf"), dtype=torch.float32, device=dev)
+    cand[o2[m], rank[m]] = c2[m].to(torch.int32)
+    cdist[o2[m], rank[m]] = w2[m]
+    return cand.cpu().numpy(), cdist.cpu().numpy()
+
+
+def build_pruned_graph(x, R=32, k=64, cap=128):
+    """Occlusion prune (to R) of the union of forward and reverse k-NN
+    candidates, then reverse fill to R."""
     ids, dd = knn_lists(x, k)
-    pruned = occlusion_prune(x, ids, dd, R)
+    cand, cdist = union_candidates(ids, dd, cap)
+    pruned = occlusion_prune(x, cand, cdist, R)
     return reverse_fill(x, pruned, R), ids
 
 
@@ -383,7 +428,7 @@ def _load_or_build(spec: dict, fn):
 def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | None = None,
                   components: int | None = None, cache: bool = True) -> Workload:
     """Build (or load from the cache) a seeded workload of the given shape."""
-    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 3}
+    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 4}
 
     def gen():
         if kind == "tiny":
