@@ -184,9 +184,12 @@ def run_ours(args):
     w = synth.make_workload("sift", args.n, args.nq)
     log(f"workload ready in {time.time() - t_setup:.1f}s (repaired links {w.meta['repaired_links']})")
     gt = exact_topk_gpu(w.base, w.queries, K, torch)
+    torch.cuda.empty_cache()
     log("ground truth ready")
-    ix32 = Index(w.base, w.adj, w.entry, storage="f32")
-    ix16 = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True)
+    wanted = args.forms.split(",")
+    need32 = "plain_f32" in wanted or not args.skip_single
+    ix32 = Index(w.base, w.adj, w.entry, storage="f32") if need32 else None
+    ix16 = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True) if "batched_bf16_rerank" in wanted else None
     q = torch.from_numpy(w.queries).cuda()
     nq = q.shape[0]
     stream = torch.cuda.current_stream()
@@ -195,7 +198,7 @@ def run_ours(args):
         "batched_bf16_rerank": (ix16, dict(rerank=True, persistent=True), 2),
         "plain_f32": (ix32, dict(), 4),
     }
-    forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
+    forms = {k: v for k, v in forms.items() if k in wanted}
     head_name = next(iter(forms))
 
     # ---- operating points: cheapest (L, M) reaching each recall target
