@@ -195,6 +195,69 @@ int ann_search_host_noalloc(const ann_index *index, const float *queries, int64_
 /* Message of the last failing call on this thread ("" if none). */
 const char *ann_last_error(void);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching (no counterpart in the paper, which processes one
+ * query at a time, Sec. 5). Requests are submitted one at a time from the
+ * host and admitted to the GPU as request groups free up. A group is a
+ * block of device-resident request state (queries, per-request k / L / M,
+ * results, counters) for max_batch requests; `streams` groups exist, so at
+ * most streams * max_batch requests are on the device at once, and the
+ * device memory they take is the admission budget. The library's scheduler
+ * thread fills any free group with the waiting requests and launches it on
+ * that group's own stream, so requests that arrive while others are on the
+ * GPU run alongside them. In sync mode each result is exactly the result of
+ * a single ann_search_ex of that query with the same k, L, M and params. */
+
+typedef struct {
+    int32_t slots;          /* requests accepted and not yet collected; 0 = 4 * streams * max_batch */
+    int32_t max_batch;      /* requests per launch (one group); 0 = 1024 */
+    int32_t streams;        /* groups, i.e. launches in flight at once; 0 = 4 */
+    int32_t max_k;          /* per-request limits; 0 = 100 / 1024 / 32 */
+    int32_t max_L;
+    int32_t max_M;
+    int32_t mode;           /* ann_mode for every request */
+    int32_t rerank;         /* as in ann_search_params */
+    int64_t scratch_bytes;  /* cap on the device bytes of all groups; 0 = no cap.
+                             * streams is lowered until the groups fit. */
+} ann_serve_config;
+
+typedef struct ann_server ann_server;
+
+typedef struct {
+    uint64_t tag;             /* the caller's tag from ann_serve_submit */
+    int32_t k;                /* valid entries in ids / dists */
+    int32_t status;           /* ANN_OK or the request's error */
+    double latency_us;        /* submit to completion, host clock */
+    double device_us;         /* the query's own time on the device */
+    int64_t device_start_ns;  /* device globaltimer at the query's start and end */
+    int64_t device_end_ns;
+} ann_result;
+
+/* Create a server over an index (the index must outlive the server). The
+ * index's device must be current. Errors: ANN_ERR_ARG for limits outside
+ * those of ann_search_ex, ANN_ERR_OOM, ANN_ERR_CUDA. */
+int ann_serve_create(const ann_index *index, const ann_serve_config *cfg, ann_server **out);
+
+/* Finish every accepted request, stop the scheduler and free everything.
+ * Results not yet collected are dropped. NULL is a no-op. */
+void ann_serve_destroy(ann_server *server);
+
+/* Submit one query (host pointer to d float32, copied before return) with
+ * its own k, L, M and a caller tag. Never blocks: returns ANN_ERR_BUSY when
+ * `slots` requests are already accepted and not yet collected, ANN_ERR_ARG
+ * for k, L, M outside the config (or k > L). Thread safe. */
+int ann_serve_submit(ann_server *server, const float *query, int32_t k, int32_t L, int32_t M,
+                     uint64_t tag);
+
+/* Collect up to max completed requests (completion order). results[i]
+ * describes request i; its ids / dists are written to
+ * out_ids + i * cfg.max_k and out_dists + i * cfg.max_k (host; entries past
+ * results[i].k are padded with -1 / +inf). Waits at most timeout_us
+ * microseconds for the first completion and returns the number collected
+ * (>= 1), or ANN_ERR_TIMEOUT when nothing completed in time. Thread safe. */
+int ann_serve_poll(ann_server *server, ann_result *results, int64_t *out_ids, float *out_dists,
+                   int32_t max, int32_t timeout_us);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,18 @@ class SearchParams(ctypes.Structure):
                 ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("max_k", ctypes.c_int32), ("max_L", ctypes.c_int32), ("max_M", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("rerank", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("k", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("latency_us", ctypes.c_double), ("device_us", ctypes.c_double),
+                ("device_start_ns", ctypes.c_int64), ("device_end_ns", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -77,6 +89,11 @@ def lib():
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp,
                                                   ctypes.POINTER(SearchParams), vp]
+            L.ann_serve_create.argtypes = [vp, ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
+            L.ann_serve_destroy.argtypes = [vp]
+            L.ann_serve_destroy.restype = None
+            L.ann_serve_submit.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint64]
+            L.ann_serve_poll.argtypes = [vp, ctypes.POINTER(Result), vp, vp, i32, i32]
             L.ann_last_error.restype = ctypes.c_char_p
             L.ann_last_error.argtypes = []
             _lib = L
@@ -125,3 +142,32 @@ def ann_search_host(index, queries, nq, k, L, M, out_ids, out_dists, params, str
 def ann_search_host_noalloc(index, queries, nq, k, L, M, out_ids, out_dists, params, stream) -> None:
     p = ctypes.byref(params) if params is not None else None
     _check(lib().ann_search_host_noalloc(index, queries, nq, k, L, M, out_ids, out_dists, p, stream))
+
+
+def ann_serve_create(index, cfg) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().ann_serve_create(index, ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def ann_serve_destroy(server) -> None:
+    lib().ann_serve_destroy(server)
+
+
+def ann_serve_submit(server, query, k, L, M, tag) -> int:
+    """Returns ANN_OK or ANN_ERR_BUSY (a full server is not an error for the
+    caller); raises on any other status."""
+    rc = lib().ann_serve_submit(server, query, k, L, M, tag)
+    if rc not in (ANN_OK, ANN_ERR_BUSY):
+        _check(rc)
+    return rc
+
+
+def ann_serve_poll(server, results, out_ids, out_dists, max_n, timeout_us) -> int:
+    """Returns the number of completions (0 on timeout); raises on errors."""
+    rc = lib().ann_serve_poll(server, results, out_ids, out_dists, max_n, timeout_us)
+    if rc == ANN_ERR_TIMEOUT:
+        return 0
+    if rc < 0:
+        _check(rc)
+    return rc

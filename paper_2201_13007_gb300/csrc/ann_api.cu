@@ -200,12 +200,14 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
             return fail(ANN_ERR_ARG, "threads=%d not in {64,...,1024}", threads);
         if (threads / 32 < M) return fail(ANN_ERR_ARG, "async mode needs threads >= 32*M");
     } else {
-        if (threads == 0) threads = (M * x.R >= 256) ? 256 : 128;
+        // measured on the 1M x 128 workload: long queues want more warps per
+        // query (more rows in flight per step), short ones more queries per SM
+        if (threads == 0) threads = L >= 384 ? 512 : (M * x.R >= 1024 ? 256 : 128);
         if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
             return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
     }
     int hb = p->hash_bits;
-    if (hb == 0) hb = L > 512 ? 14 : 13;
+    if (hb == 0) hb = L >= 384 ? 14 : (M * x.R >= 1024 ? 13 : 12);
     if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
 
     ann::SearchArgs &a = plan->a;
@@ -244,8 +246,13 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (a.rerank && L > need) need = L;
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
-    int smem = async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, a.hash_bits)
-                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M).total;
+    auto smem_for = [&](int bits) {
+        return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M).total;
+    };
+    int smem = smem_for(a.hash_bits);
+    // an automatic visited table shrinks until the layout fits (it may then forget more often)
+    while (p->hash_bits == 0 && smem > max_dyn_smem() && a.hash_bits > 10) smem = smem_for(--a.hash_bits);
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
                     smem, max_dyn_smem());
@@ -280,6 +287,10 @@ int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace ann {
+void set_error(const char *msg) { g_err = msg; }
+}  // namespace ann
 
 extern "C" {
 

@@ -115,6 +115,9 @@ cudaError_t launch_async_search(const SearchArgs &a, int storage, int threads, i
 cudaError_t async_search_occupancy(int storage, int threads, int smem_bytes, int *blocks_per_sm);
 int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits);
 
+// ann_api.cu: sets the calling thread's ann_last_error() text
+void set_error(const char *msg);
+
 // encode.cu
 cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, void *dst, int32_t d_pad,
                           float *scales, cudaStream_t stream);

@@ -49,3 +49,7 @@ def test_argument_errors_without_gpu():
     assert "NULL" in ann.ann_last_error()
     with pytest.raises(ann.AnnError):
         ann.ann_search(None, None, 1, 1, 1, 1, None, None, None)
+    from paper_2201_13007_gb300 import _abi
+    with pytest.raises(ann.AnnError):
+        _abi.ann_serve_create(None, None)
+    assert "NULL" in ann.ann_last_error()
