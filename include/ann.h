@@ -109,6 +109,11 @@ typedef struct {
     const int32_t *L_per_query;
     const int32_t *M_per_query;
     ann_query_stats *stats; /* device array of nq, or NULL */
+    /* Work list (device int32 array of nq entries, or NULL): the search runs
+     * query order[i] for i in [0, nq); query, per-query, stats and output
+     * arrays are indexed by the query number and must be large enough for
+     * every number in the list. NULL runs queries 0..nq-1. */
+    const int32_t *order;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").
@@ -191,6 +196,46 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
 int ann_search_host_noalloc(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
                             int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
                             void *stream);
+
+/* ------------------------------------------------------------ batching
+ * A planned batch of queries with uneven k, L, M (no counterpart in the
+ * paper, which runs one query at a time). Queries are grouped into buckets
+ * by L; each bucket is one persistent grid, sized for the bucket's largest L
+ * and M, that pulls its queries longest-first from a device work list. The
+ * buckets run concurrently on the plan's own streams, forked from and joined
+ * back into the caller's stream, so a whole ann_batch_search can be captured
+ * into a CUDA graph (it allocates nothing and never synchronises). */
+
+typedef struct {
+    int32_t L_max;      /* the bucket takes queries with L <= L_max (after smaller buckets) */
+    int32_t threads;    /* launch config for the bucket; 0 = the ann_search_ex default */
+    int32_t hash_bits;
+} ann_bucket_config;
+
+typedef struct ann_batch ann_batch;
+
+/* Plan nq queries. k, L, M are HOST int32 arrays of nq entries (each with
+ * 1 <= k <= L <= 2048, 1 <= M <= 64). buckets: n_buckets configs in
+ * ascending L_max, or NULL for the ladder 32, 64, 128, 256, 512, 1024, 2048
+ * with default launch configs. params supplies mode, schedule, re-rank and an
+ * optional stats array (its per-query arrays and order must be NULL). The
+ * plan keeps device copies of k, L, M and of the work lists; the index must
+ * outlive it. Errors: ANN_ERR_ARG, ANN_ERR_OOM, ANN_ERR_CUDA. */
+int ann_batch_create(const ann_index *index, int64_t nq, const int32_t *k, const int32_t *L, const int32_t *M,
+                     const ann_bucket_config *buckets, int32_t n_buckets, const ann_search_params *params,
+                     ann_batch **out);
+
+/* Run the planned batch on stream. queries: device nq x d; out_ids / out_dists:
+ * device nq x k_max with k_max = the largest k in the plan (entries past a
+ * query's own k hold -1 / +inf). Asynchronous. Calls on one plan must not
+ * overlap on the GPU (the plan's work counters are reset by each call). */
+int ann_batch_search(ann_batch *batch, const float *queries, int64_t *out_ids, float *out_dists, void *stream);
+
+/* Number of non-empty buckets and the largest k of a plan. */
+int ann_batch_info(const ann_batch *batch, int32_t *n_buckets, int32_t *k_max);
+
+/* Free a plan (after its searches have finished). NULL is a no-op. */
+void ann_batch_destroy(ann_batch *batch);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *ann_last_error(void);

@@ -49,7 +49,12 @@ class SearchParams(ctypes.Structure):
                 ("R_ratio", ctypes.c_float), ("rerank", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("hash_bits", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
-                ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+                ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p),
+                ("order", ctypes.c_void_p)]
+
+
+class BucketConfig(ctypes.Structure):
+    _fields_ = [("L_max", ctypes.c_int32), ("threads", ctypes.c_int32), ("hash_bits", ctypes.c_int32)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -89,6 +94,12 @@ def lib():
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp,
                                                   ctypes.POINTER(SearchParams), vp]
+            L.ann_batch_create.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(BucketConfig), i32,
+                                           ctypes.POINTER(SearchParams), ctypes.POINTER(vp)]
+            L.ann_batch_search.argtypes = [vp, vp, vp, vp, vp]
+            L.ann_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+            L.ann_batch_destroy.argtypes = [vp]
+            L.ann_batch_destroy.restype = None
             L.ann_serve_create.argtypes = [vp, ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
             L.ann_serve_destroy.argtypes = [vp]
             L.ann_serve_destroy.restype = None
@@ -171,3 +182,24 @@ def ann_serve_poll(server, results, out_ids, out_dists, max_n, timeout_us) -> in
     if rc < 0:
         _check(rc)
     return rc
+
+
+def ann_batch_create(index, nq, k, L, M, buckets, n_buckets, params) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().ann_batch_create(index, nq, k, L, M, buckets, n_buckets,
+                                  ctypes.byref(params) if params is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def ann_batch_search(batch, queries, out_ids, out_dists, stream) -> None:
+    _check(lib().ann_batch_search(batch, queries, out_ids, out_dists, stream))
+
+
+def ann_batch_info(batch):
+    nb, km = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ann_batch_info(batch, ctypes.byref(nb), ctypes.byref(km)))
+    return nb.value, km.value
+
+
+def ann_batch_destroy(batch) -> None:
+    lib().ann_batch_destroy(batch)

@@ -161,14 +161,9 @@ int create_impl(const float *base, int64_t n, int32_t d, int32_t storage, const 
     return ANN_OK;
 }
 
-struct Plan {
-    ann::SearchArgs a;
-    int threads;
-    int smem;
-    int grid;
-    int mode;
-    int storage;
-};
+}  // namespace
+
+namespace ann {
 
 int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
                 int64_t *out_ids, float *out_dists, const ann_search_params *p, Plan *plan) {
@@ -241,6 +236,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.stats = p->stats;
     a.work_counter = x.work_counter;
     a.persistent = p->persistent ? 1 : 0;
+    a.order = p->order;
     a.Lcap = L;
     int need = M * x.R;
     if (a.rerank && L > need) need = L;
@@ -272,6 +268,21 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     }
     return ANN_OK;
 }
+
+cudaError_t launch(const Plan &plan, cudaStream_t s) {
+    return plan.mode == ANN_MODE_ASYNC
+               ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
+               : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
+}
+
+int index_device(const ann_index *index) { return index->d.device; }
+
+}  // namespace ann
+
+namespace {
+
+using ann::Plan;
+using ann::plan_search;
 
 int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
     if (plan.a.nq == 0) return ANN_OK;

@@ -60,6 +60,7 @@ struct SearchArgs {
     ann_query_stats *stats;
     int *work_counter;
     int32_t persistent;
+    const int32_t *order;  // work list: item i is query order[i] (nullptr: item i is query i)
     // shared-memory layout
     int32_t Lcap;        // queue capacity
     int32_t Ccap;        // candidate / sort buffer, power of two >= 32
@@ -117,6 +118,20 @@ int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits);
 
 // ann_api.cu: sets the calling thread's ann_last_error() text
 void set_error(const char *msg);
+
+// ann_api.cu: argument checks and launch configuration of one search
+struct Plan {
+    SearchArgs a;
+    int threads;
+    int smem;
+    int grid;
+    int mode;
+    int storage;
+};
+int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
+                int64_t *out_ids, float *out_dists, const ann_search_params *p, Plan *plan);
+cudaError_t launch(const Plan &plan, cudaStream_t s);
+int index_device(const ann_index *index);
 
 // encode.cu
 cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, void *dst, int32_t d_pad,

@@ -71,10 +71,13 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
     const int Lcap = a.Lcap;
 
     for (;;) {
-        if (tid == 0) ctl.qi = a.persistent ? (long long)atomicAdd(a.work_counter, 1) : (long long)blockIdx.x;
+        if (tid == 0) {
+            const int item = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
+            ctl.qi = item >= a.nq ? -1 : (a.order ? a.order[item] : item);
+        }
         __syncthreads();
         const long long qi = ctl.qi;
-        if (qi >= a.nq) break;
+        if (qi < 0) break;  // work list exhausted
         const int64_t t0 = global_ns();
         const int k = a.k_arr ? a.k_arr[qi] : a.k;
         const int L = a.L_arr ? a.L_arr[qi] : a.L;

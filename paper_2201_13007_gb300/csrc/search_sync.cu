@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
 
     for (;;) {
         if (tid == 0) {
-            ctl.qi = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
+            const int item = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
+            ctl.qi = item >= a.nq ? -1 : (a.order ? a.order[item] : item);
             ctl.t0 = global_ns();
             ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
             ctl.evals = 1;
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         }
         __syncthreads();
         const int qi = ctl.qi;
-        if (qi >= a.nq) break;
+        if (qi < 0) break;  // work list exhausted
 
         const int k = a.k_arr ? a.k_arr[qi] : a.k;
         const int L = a.L_arr ? a.L_arr[qi] : a.L;

@@ -63,11 +63,12 @@ class Index:
 
     @staticmethod
     def params(mode="sync", M0=1, t=1, R_ratio=0.8, rerank=False, threads=0, hash_bits=0,
-               persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None):
+               persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None,
+               order=None):
         return _abi.SearchParams(mode=_abi.MODE[mode], M0=M0, t=t, R_ratio=R_ratio, rerank=int(rerank),
                                  threads=threads, hash_bits=hash_bits, persistent=int(persistent),
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
-                                 M_per_query=_ptr(M_per_query), stats=_ptr(stats))
+                                 M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order))
 
     def search(self, queries, k, L, M, *, out=None, stream=None, with_stats=False, stats=None, **kw):
         """queries: CUDA float32 nq x d. Returns (ids int64, dists float32[, stats int64 nq x 8]).
@@ -105,6 +106,49 @@ class Index:
         _abi.ann_search_host(self.handle, _ptr(q), nq, k, L, M, _ptr(ids), _ptr(dists), p,
                              _stream_handle(stream))
         return ids, dists
+
+
+class Batch:
+    """A planned batch of queries with uneven k, L, M (ann_batch_create).
+    k, L, M: host integer arrays; buckets: None or a list of
+    (L_max, threads, hash_bits) tuples (e.g. from autotune.tune_buckets)."""
+
+    def __init__(self, index, k, L, M, *, buckets=None, stats=None, **params):
+        self.k = np.ascontiguousarray(k, np.int32)
+        self.L = np.ascontiguousarray(L, np.int32)
+        self.M = np.ascontiguousarray(M, np.int32)
+        self.nq = self.k.shape[0]
+        self.index = index
+        nb = 0
+        cfg = None
+        if buckets:
+            nb = len(buckets)
+            cfg = (_abi.BucketConfig * nb)(*[_abi.BucketConfig(int(a), int(b), int(c)) for a, b, c in buckets])
+        p = Index.params(stats=stats, **params)
+        vp = lambda a: ctypes_void(a.ctypes.data)
+        self._h = _abi.ann_batch_create(index.handle, self.nq, vp(self.k), vp(self.L), vp(self.M), cfg, nb, p)
+        self.n_buckets, self.k_max = _abi.ann_batch_info(ctypes_void(self._h))
+
+    def search(self, queries, out=None, stream=None):
+        q = queries.contiguous()
+        if out is None:
+            ids = torch.empty((self.nq, self.k_max), dtype=torch.int64, device=q.device)
+            dists = torch.empty((self.nq, self.k_max), dtype=torch.float32, device=q.device)
+        else:
+            ids, dists = out
+        _abi.ann_batch_search(ctypes_void(self._h), _ptr(q), _ptr(ids), _ptr(dists), _stream_handle(stream))
+        return ids, dists
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.ann_batch_destroy(ctypes_void(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats_dict(stats):
