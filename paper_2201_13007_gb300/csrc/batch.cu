@@ -143,12 +143,13 @@ int ann_batch_create(const ann_index *index, int64_t nq, const int32_t *k, const
         if (cfg[b].threads) p.threads = cfg[b].threads;
         if (cfg[b].hash_bits) p.hash_bits = cfg[b].hash_bits;
         // device pointers for queries / outputs are bound at search time
-        int rc = ann::plan_search(index, reinterpret_cast<const float *>(16), n, kmax, Lm, Mm,
+        int rc = ann::plan_search(index, reinterpret_cast<const float *>(16), n, std::min(kmax, Lm), Lm, Mm,
                                   reinterpret_cast<int64_t *>(16), reinterpret_cast<float *>(16), &p, &bk.plan);
         if (rc != ANN_OK) {
             free_batch(bt);
             return rc;
         }
+        bk.plan.a.k = kmax;  // output row stride (and per-query k bound) of the whole batch
         bk.plan.a.work_counter = bt->d_counters + bt->buckets.size();
         e = cudaStreamCreateWithFlags(&bk.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bk.joined, cudaEventDisableTiming);

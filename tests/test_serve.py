@@ -32,18 +32,23 @@ def _server(ix, **kw):
     return ctypes.c_void_p(_abi.ann_serve_create(ix.handle, cfg))
 
 
-def _drain(srv, n, kmax, timeout_s=60.0):
+def _collect(srv, out, kmax, timeout_us):
     res = (_abi.Result * 64)()
     ids = np.zeros((64, kmax), np.int64)
     dists = np.zeros((64, kmax), np.float32)
-    out = {}
+    got = _abi.ann_serve_poll(srv, res, _vp(ids), _vp(dists), 64, timeout_us)
+    for i in range(got):
+        r = res[i]
+        out[r.tag] = (r.status, r.k, ids[i, :r.k].copy(), dists[i, :r.k].copy(), r.latency_us, r.device_us,
+                      r.device_start_ns, r.device_end_ns)
+    return got
+
+
+def _drain(srv, n, kmax, timeout_s=60.0, out=None):
+    out = {} if out is None else out
     t0 = time.time()
     while len(out) < n and time.time() - t0 < timeout_s:
-        got = _abi.ann_serve_poll(srv, res, _vp(ids), _vp(dists), 64, 100000)
-        for i in range(got):
-            r = res[i]
-            out[r.tag] = (r.status, r.k, ids[i, :r.k].copy(), dists[i, :r.k].copy(), r.latency_us, r.device_us,
-                          r.device_start_ns, r.device_end_ns)
+        _collect(srv, out, kmax, 100000)
     return out
 
 
@@ -56,12 +61,14 @@ def test_each_result_equals_its_standalone_search(setup):
     Ls = np.maximum(ks, g.choice([16, 32, 64, 128], n))
     Ms = g.choice([1, 2, 4, 8], n)
     srv = _server(ix, max_batch=8, streams=4, max_k=20, max_L=128, max_M=8)
+    out = {}
     try:
         for t in range(n):
             q = np.ascontiguousarray(w.queries[qi[t]])
+            # a full server (every slot submitted and not yet collected) answers BUSY: collect, then retry
             while _abi.ann_serve_submit(srv, _vp(q), int(ks[t]), int(Ls[t]), int(Ms[t]), t) == _abi.ANN_ERR_BUSY:
-                time.sleep(0.0005)
-        out = _drain(srv, n, 20)
+                _collect(srv, out, 20, 1000)
+        _drain(srv, n, 20, out=out)
     finally:
         _abi.ann_serve_destroy(srv)
     assert len(out) == n
@@ -114,10 +121,11 @@ def test_scratch_budget_limits_groups(setup):
     srv = _server(ix, max_batch=8, streams=8, max_k=10, max_L=32, max_M=2, scratch_bytes=3 * per_group)
     try:
         q = np.ascontiguousarray(w.queries[1])
+        out = {}
         for t in range(40):
             while _abi.ann_serve_submit(srv, _vp(q), 10, 32, 2, t) == _abi.ANN_ERR_BUSY:
-                time.sleep(0.0005)
-        out = _drain(srv, 40, 10)
+                _collect(srv, out, 10, 1000)
+        _drain(srv, 40, 10, out=out)
         assert len(out) == 40
         first = out[0][2]
         for v in out.values():
