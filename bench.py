@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-single", action="store_true")
+    ap.add_argument("--workload", default="sift", choices=["sift", "gist", "deep-batch", "serve"],
+                    help="sift: the headline (default); the others measure the precision, batching and serving "
+                         "workloads and print one JSON line each")
     return ap.parse_args()
 
 
@@ -78,16 +81,19 @@ def recall_at_k(ids, gt):
     return hits / gt.size
 
 
-def exact_topk_gpu(base, queries, k, torch):
-    """Exact top-k by FP64 L2 on the GPU with torch (recall ground truth);
-    ties broken by id."""
+def exact_topk_gpu(base, queries, k, torch, metric="l2"):
+    """Exact top-k by FP64 L2 (or -inner product) on the GPU with torch
+    (recall ground truth); ties broken by id."""
     dev = torch.device("cuda")
     X = torch.from_numpy(base).to(dev, torch.float64)
     xn = (X * X).sum(1)
     out = np.empty((queries.shape[0], k), np.int64)
     for a in range(0, queries.shape[0], 1024):
         Q = torch.from_numpy(queries[a:a + 1024]).to(dev, torch.float64)
-        D = (Q * Q).sum(1, keepdim=True) + xn[None, :] - 2.0 * (Q @ X.T)
+        if metric == "l2":
+            D = (Q * Q).sum(1, keepdim=True) + xn[None, :] - 2.0 * (Q @ X.T)
+        else:
+            D = -(Q @ X.T)
         v, i = torch.topk(D, k + 8, dim=1, largest=False, sorted=True)
         v, i = v.cpu().numpy(), i.cpu().numpy()
         for r in range(v.shape[0]):
@@ -434,10 +440,278 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ helpers
+
+def event_time(torch, fn, steps, warmup, flush=None):
+    """Per-step device seconds of fn() with CUDA events on the current stream."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    s = torch.cuda.current_stream()
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3)
+    return out
+
+
+def cheapest_points(torch, search, q, gt, Ls, Ms, targets, k=K):
+    """(L, M) with the shortest single run reaching each recall target."""
+    seen = {}
+    for M in Ms:
+        for L in Ls:
+            if L < k:
+                continue
+            ids = search(q, L, M)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ids = search(q, L, M)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rec = recall_at_k(ids.cpu().numpy()[:, :k], gt[:, :k])
+            seen[(L, M)] = (rec, dt)
+            if rec >= max(targets) + 0.003:
+                break
+    pts = {}
+    for tgt in targets:
+        ok = [(dt, L, M, rec) for (L, M), (rec, dt) in seen.items() if rec >= tgt]
+        if not ok:
+            rec, ndt, L, M = max((rec, -dt, L, M) for (L, M), (rec, dt) in seen.items())
+            ok = [(0.0, L, M, rec)]
+        dt, L, M, rec = min(ok)
+        pts[tgt] = (L, M, rec)
+    return pts
+
+
+# --------------------------------------------- precision at high dimension
+
+def run_gist(args):
+    """1M x 960 log-normal mixture (GIST1M stand-in), 1,000 queries, L2, k=10:
+    FP16 and FP8-E4M3 (per-vector scale) storage with FP32 re-rank against
+    FP32 storage; recall and key error against FP64."""
+    import torch
+    from paper_2201_13007_gb300 import synth
+    from paper_2201_13007_gb300.index import Index
+    t0 = time.time()
+    w = synth.make_workload("gist", 1_000_000, 1000)
+    log(f"gist workload ready in {time.time() - t0:.0f}s")
+    gt = exact_topk_gpu(w.base, w.queries, K, torch)
+    torch.cuda.empty_cache()
+    q = torch.from_numpy(w.queries).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    hbm, peak_kind = peaks()
+    forms = {"f16_rerank": ("f16", True, 2), "e4m3_rerank": ("e4m3", True, 1), "f32": ("f32", False, 4)}
+    out = {"workload": "gist-like 1M x 960 (log-normal 32-component mixture), degree-32 graph, 1,000 queries, k=10, L2",
+           "peak_gbs": hbm, "peak_kind": peak_kind, "points": {}}
+    Ls = (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
+    for name, (stor, rr, es) in forms.items():
+        ix = Index(w.base, w.adj, w.entry, storage=stor, keep_f32=rr)
+        search = lambda qq, L, M: ix.search(qq, K, L, M, rerank=rr, persistent=True)[0]
+        pts = cheapest_points(torch, search, q, gt, Ls, (4, 8, 16), TARGETS)
+        for tgt, (L, M, rec) in pts.items():
+            st = torch.empty((q.shape[0], 8), dtype=torch.int64, device="cuda")
+            ids, dd = ix.search(q, K, L, M, rerank=rr, persistent=True, stats=st)
+            times = event_time(torch, lambda: ix.search(q, K, L, M, rerank=rr, persistent=True), args.steps,
+                               args.warmup, flush)
+            t = float(np.mean(times))
+            sn = st.cpu().numpy()
+            idn = ids.cpu().numpy()
+            k64 = np.stack([((w.base[idn[i]].astype(np.float64) - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                            for i in range(idn.shape[0])])
+            kerr = np.abs(dd.cpu().numpy().astype(np.float64) - k64) / np.maximum(k64, 1e-30)
+            row = ix.info()["d_pad"] * es + (4 if stor == "e4m3" else 0)
+            b = algorithmic_bytes(sn, w.R, row, w.d, K, L if rr else 0)
+            # the same point without re-rank: reduced-precision keys against FP64
+            ids_nr, d_nr = ix.search(q, K, L, M, persistent=True)
+            inr = ids_nr.cpu().numpy()
+            k64nr = np.stack([((w.base[inr[i]].astype(np.float64) - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                              for i in range(inr.shape[0])])
+            kerr_nr = np.abs(d_nr.cpu().numpy().astype(np.float64) - k64nr) / np.maximum(k64nr, 1e-30)
+            out["points"][f"{name}@{tgt}"] = {
+                "L": L, "M": M, "recall@10": recall_at_k(idn, gt), "recall@10_no_rerank": recall_at_k(inr, gt),
+                "qps": q.shape[0] / t, "ms_per_step": t * 1e3, "gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
+                "key_rel_err_max": float(kerr.max()), "key_rel_err_mean": float(kerr.mean()),
+                "stored_key_rel_err_max": float(kerr_nr.max()), "stored_key_rel_err_mean": float(kerr_nr.mean()),
+                "evals_per_query": float(sn[:, 2].mean())}
+            log(name, tgt, out["points"][f"{name}@{tgt}"])
+        ix.close()
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------- batching
+
+def run_deep_batch(args):
+    """1M x 96 L2-normalised mixture (DEEP stand-in, inner product), 100,000
+    queries with uneven k in {1,10,100}, L in {32..1024} (L >= k), M in
+    {1..32}: one planned batch (L buckets, longest-first work lists,
+    autotuned launch configs) replayed from a CUDA graph, against one launch
+    per query."""
+    import torch
+    from paper_2201_13007_gb300 import autotune, synth
+    from paper_2201_13007_gb300.index import Batch, Index
+    nq = 100_000
+    t0 = time.time()
+    w = synth.make_workload("deep", 1_000_000, nq)
+    log(f"deep workload ready in {time.time() - t0:.0f}s")
+    g = np.random.Generator(np.random.PCG64(4))
+    k = g.choice([1, 10, 100], nq).astype(np.int32)
+    Lc = np.array([32, 64, 128, 256, 512, 1024])
+    L = g.choice(Lc, nq)
+    while (L < k).any():
+        bad = L < k
+        L[bad] = g.choice(Lc, int(bad.sum()))
+    L = L.astype(np.int32)
+    M = g.choice([1, 2, 4, 8, 16, 32], nq).astype(np.int32)
+    ix = Index(w.base, w.adj, w.entry, metric="ip")
+    q = torch.from_numpy(w.queries).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    cfg = autotune.tune_buckets(ix, q, k, L, M, sample=2000, reps=2)
+    tune_s = time.time() - t0
+    log("tuned buckets", cfg, f"{tune_s:.1f}s")
+    b = Batch(ix, k, L, M, buckets=cfg)
+    ids, dists = b.search(q)
+    torch.cuda.synchronize()
+    plain = Batch(ix, k, L, M)
+    # captured once, replayed per step
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.search(q, out=(ids, dists), stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.search(q, out=(ids, dists))
+    t_graph = event_time(torch, graph.replay, args.steps, args.warmup, flush)
+    t_tuned = event_time(torch, lambda: b.search(q, out=(ids, dists)), args.steps, args.warmup, flush)
+    t_plain = event_time(torch, lambda: plain.search(q), args.steps, args.warmup, flush)
+    # recall on a sample (exact top-100 by FP64 inner product)
+    sample = np.arange(0, nq, 50)
+    gt = exact_topk_gpu(w.base, w.queries[sample], 100, torch, metric="ip")
+    idn = ids.cpu().numpy()
+    rec = np.mean([len(set(idn[i, :k[i]].tolist()) & set(gt[j, :k[i]].tolist())) / k[i]
+                   for j, i in enumerate(sample)])
+    # one launch per query on a subset
+    sub = np.arange(0, nq, 100)
+    lat = []
+    for i in sub:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.search(q[i:i + 1], int(k[i]), int(L[i]), int(M[i]))
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1) * 1e3)
+    out = {"workload": "deep-like 1M x 96 unit vectors (inner product), 100,000 queries, k in {1,10,100}, "
+                       "L in {32..1024}, M in {1..32}",
+           "buckets": cfg, "tune_s": tune_s,
+           "graph_replay": {"qps": nq / float(np.mean(t_graph)), "ms_per_step": float(np.mean(t_graph)) * 1e3},
+           "tuned_no_graph": {"qps": nq / float(np.mean(t_tuned))},
+           "default_buckets": {"qps": nq / float(np.mean(t_plain))},
+           "one_launch_per_query": {"qps": 1e6 / float(np.mean(lat)), "p50_us": float(np.percentile(lat, 50)),
+                                    "p99_us": float(np.percentile(lat, 99)), "sample": int(sub.size)},
+           "mean_recall@k_sample": float(rec), "recall_sample": int(sample.size)}
+    print(json.dumps(out))
+
+
+# -------------------------------------------------------------- serving
+
+def run_serve(args):
+    """Continuous-batching server under Poisson arrivals: 1M x 96 BF16 unit
+    vectors (inner product), k in {10, 100}; latency percentiles at five
+    offered rates (0.1 .. 0.9 of the measured saturation rate)."""
+    import ctypes
+    import threading as th
+    import torch
+    from paper_2201_13007_gb300 import _abi, synth
+    from paper_2201_13007_gb300.index import Index
+    w = synth.make_workload("deep", 1_000_000, 20_000, components=256)
+    ix = Index(w.base, w.adj, w.entry, storage="bf16", metric="ip")
+    gt = exact_topk_gpu(w.base, w.queries[:2000], 100, torch, metric="ip")
+    qd = torch.from_numpy(w.queries[:2000]).cuda()
+    pts = {}
+    for kk in (10, 100):
+        search = lambda qq, L, M: ix.search(qq, kk, L, M, persistent=True)[0]
+        pts[kk] = cheapest_points(torch, search, qd, gt[:, :kk], (100, 128, 160, 192, 256, 384, 512, 768, 1024),
+                                  (8, 16), TARGETS, k=kk)
+    log("serving points", pts)
+    g = np.random.Generator(np.random.PCG64(5))
+    nreq = 20_000
+    ks = g.choice([10, 100], nreq)
+    tg = g.choice(TARGETS, nreq)
+    qi = g.integers(0, w.queries.shape[0], nreq)
+    LL = np.array([pts[int(k_)][float(t_)][0] for k_, t_ in zip(ks, tg)], np.int32)
+    MM = np.array([pts[int(k_)][float(t_)][1] for k_, t_ in zip(ks, tg)], np.int32)
+    cfg = _abi.ServeConfig(max_batch=512, streams=4, max_k=100, max_L=int(LL.max()), max_M=16)
+    res_all = []
+
+    def run(rate):
+        srv = ctypes.c_void_p(_abi.ann_serve_create(ix.handle, cfg))
+        done = []
+        stop = th.Event()
+
+        def poller():
+            res = (_abi.Result * 256)()
+            ids = np.zeros((256, 100), np.int64)
+            d = np.zeros((256, 100), np.float32)
+            while not (stop.is_set() and len(done) >= nreq):
+                got = _abi.ann_serve_poll(srv, res, ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(d.ctypes.data),
+                                          256, 2000)
+                for i in range(got):
+                    done.append((res[i].latency_us, res[i].device_us))
+        pt = th.Thread(target=poller)
+        pt.start()
+        arr = np.cumsum(g.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq)
+        t0 = time.perf_counter()
+        busy = 0
+        for i in range(nreq):
+            while rate and time.perf_counter() - t0 < arr[i]:
+                pass
+            qv = w.queries[qi[i]]
+            while _abi.ann_serve_submit(srv, ctypes.c_void_p(qv.ctypes.data), int(ks[i]), int(LL[i]), int(MM[i]), i) \
+                    == _abi.ANN_ERR_BUSY:
+                busy += 1
+        stop.set()
+        pt.join()
+        wall = time.perf_counter() - t0
+        _abi.ann_serve_destroy(srv)
+        lat = np.array([x[0] for x in done])
+        dev = np.array([x[1] for x in done])
+        return {"offered_qps": rate, "achieved_qps": nreq / wall, "p50_us": float(np.percentile(lat, 50)),
+                "p99_us": float(np.percentile(lat, 99)), "device_p50_us": float(np.percentile(dev, 50)),
+                "device_p99_us": float(np.percentile(dev, 99)), "busy_retries": busy}
+
+    sat = run(0)  # flood: every request submitted as fast as the client can
+    log("saturation", sat)
+    for f in (0.1, 0.3, 0.5, 0.7, 0.9):
+        r = run(f * sat["achieved_qps"])
+        res_all.append(r)
+        log(f, r)
+    out = {"workload": "deep-like 1M x 96 BF16 unit vectors (inner product), 256 components, k in {10,100}, "
+                       "recall targets 0.9/0.99 mapped to L; Poisson arrivals",
+           "points": {str(k_): {str(t_): v for t_, v in d.items()} for k_, d in pts.items()},
+           "saturation": sat, "rates": res_all,
+           "client": "one Python thread submitting through ctypes, one polling"}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "gist":
+        run_gist(args)
+    elif args.workload == "deep-batch":
+        run_deep_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
