@@ -24,9 +24,13 @@ Workload recipes (n x d, components, distribution):
   them is navigable: recall@10 stays below 0.75 at L = 256.)
 - ``gist``   n x 960 non-negative: 32 components, x = exp(mu_c + 0.5 z),
   mu_c ~ N(-2, 0.5)^960; graph as ``sift``.
-- ``deep``   n x 96 L2-normalised: ``components`` components (128 by
-  default), means N(0,1)^96, sigma 0.3, then normalised; inner-product search;
-  graph built with L2 on the unit vectors (equivalent ordering to -IP).
+- ``deep``   n x 96 L2-normalised, low intrinsic dimension: a
+  ``components``-component (128 by default) mixture in a 32-d latent space
+  mapped to 96-d by a fixed random matrix, plus noise 0.1, normalised;
+  inner-product search; graph built with L2 on the unit vectors (the same
+  ordering as -IP). (An isotropic 96-d mixture is either islands (small
+  sigma) or nearly uniform on the sphere (large sigma); neither is navigable
+  like DEEP descriptors: recall@10 stays below 0.6 at L = 512.)
 
 The entry point is the base point nearest (FP64 L2) to the mean of the base
 set, ties to the smaller id (a cheap stand-in for the medoid).
@@ -118,16 +122,23 @@ def mixture_gist(n, nq, d=960, C=32, seed=300):
     return draw(n, seed + 1), draw(nq, seed + 2)
 
 
-def mixture_deep(n, nq, d=96, C=128, sigma=0.3, seed=400):
-    means = _rng(seed + 7).standard_normal((C, d))
+def mixture_deep(n, nq, d=96, C=128, r=32, spread=1.0, noise=0.1, seed=400):
+    """Unit vectors with low intrinsic dimension: a C-component mixture in an
+    r-dimensional latent space (means N(0, spread^2), unit spread around
+    them), mapped to d dimensions by a fixed random matrix, plus isotropic
+    noise, then L2-normalised."""
+    g = _rng(seed + 7)
+    means = g.standard_normal((C, r)) * spread
+    A = g.standard_normal((d, r)) / np.sqrt(r)
     def draw(count, s):
-        r = _rng(s)
-        lab = _labels(r, count, C)
+        rr = _rng(s)
+        lab = _labels(rr, count, C)
         out = np.empty((count, d), np.float32)
         step = 1 << 16
         for a in range(0, count, step):
             b = min(count, a + step)
-            v = means[lab[a:b]] + sigma * r.standard_normal((b - a, d))
+            z = means[lab[a:b]] + rr.standard_normal((b - a, r))
+            v = z @ A.T + noise * rr.standard_normal((b - a, d))
             v /= np.linalg.norm(v, axis=1, keepdims=True)
             out[a:b] = v
         return out
@@ -428,7 +439,7 @@ def _load_or_build(spec: dict, fn):
 def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | None = None,
                   components: int | None = None, cache: bool = True) -> Workload:
     """Build (or load from the cache) a seeded workload of the given shape."""
-    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 4}
+    spec = {"kind": kind, "n": n, "nq": nq, "d": d, "R": R, "components": components, "v": 5}
 
     def gen():
         if kind == "tiny":
