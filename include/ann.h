@@ -114,6 +114,11 @@ typedef struct {
      * arrays are indexed by the query number and must be large enough for
      * every number in the list. NULL runs queries 0..nq-1. */
     const int32_t *order;
+    /* Sync mode only: spread each query over a thread-block cluster of this
+     * many CTAs (2, 4 or 8) that share the step's work through distributed
+     * shared memory (lower latency per query); 0 or 1 = one CTA per query.
+     * A clustered search is never persistent (one cluster per query). */
+    int32_t cluster;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

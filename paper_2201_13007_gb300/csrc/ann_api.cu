@@ -185,6 +185,10 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (p->rerank && !x.base32) return fail(ANN_ERR_ARG, "rerank needs an FP32 copy (ANN_INDEX_KEEP_F32)");
     if (async && !(p->R_ratio >= 0.f)) return fail(ANN_ERR_ARG, "R_ratio must be >= 0 (or INFINITY)");
     if (async && M > 32) return fail(ANN_ERR_ARG, "async mode runs one warp per walker: M=%d > 32", M);
+    const int csize = p->cluster > 1 ? p->cluster : 1;
+    if (csize != 1 && csize != 2 && csize != 4 && csize != 8)
+        return fail(ANN_ERR_ARG, "cluster=%d not in {0, 1, 2, 4, 8}", p->cluster);
+    if (csize > 1 && async) return fail(ANN_ERR_ARG, "clusters are for sync mode only");
     int threads = p->threads;
     if (async) {
         // one warp per walker: T = M walkers, at least two warps
@@ -200,6 +204,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         if (threads == 0) threads = L >= 384 ? 512 : (M * x.R >= 1024 ? 256 : 128);
         if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
             return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
+        if (csize > 1 && threads == 64) threads = 128;
     }
     int hb = p->hash_bits;
     if (hb == 0) hb = L >= 384 ? 14 : (M * x.R >= 1024 ? 13 : 12);
@@ -243,6 +248,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
     auto smem_for = [&](int bits) {
+        if (csize > 1) return ann::cluster_smem_size(a.qfloats, a.Lcap, a.Ccap, bits, M);
         return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
                      : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M).total;
     };
@@ -256,8 +262,10 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     plan->smem = smem;
     plan->mode = p->mode;
     plan->storage = x.storage;
+    plan->cluster = csize;
+    if (csize > 1) a.persistent = 0;
     plan->grid = (int)(nq > 0x7fffffff ? 0x7fffffff : nq);
-    if (a.persistent && nq > 0) {
+    if (a.persistent && csize == 1 && nq > 0) {
         int bps = 0;
         cudaError_t e = async ? ann::async_search_occupancy(x.storage, threads, smem, &bps)
                               : ann::sync_search_occupancy(x.storage, threads, smem, &bps);
@@ -270,6 +278,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
 }
 
 cudaError_t launch(const Plan &plan, cudaStream_t s) {
+    if (plan.cluster > 1)
+        return ann::launch_cluster_search(plan.a, plan.storage, plan.threads, plan.smem, plan.cluster, s);
     return plan.mode == ANN_MODE_ASYNC
                ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
                : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
@@ -290,9 +300,7 @@ int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
     cudaGetDevice(&dev);
     if (dev != index->d.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, index->d.device);
     if (plan.a.persistent) ANN_CUDA(cudaMemsetAsync(index->d.work_counter, 0, sizeof(int), s));
-    cudaError_t e = plan.mode == ANN_MODE_ASYNC
-                        ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
-                        : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
+    cudaError_t e = ann::launch(plan, s);
     if (e != cudaSuccess) return cuda_fail(e, "search launch");
     return ANN_OK;
 }

@@ -127,11 +127,17 @@ struct Plan {
     int grid;
     int mode;
     int storage;
+    int cluster;  // CTAs per query (1 = no cluster)
 };
 int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L, int32_t M,
                 int64_t *out_ids, float *out_dists, const ann_search_params *p, Plan *plan);
 cudaError_t launch(const Plan &plan, cudaStream_t s);
 int index_device(const ann_index *index);
+
+// search_cluster.cu
+cudaError_t launch_cluster_search(const SearchArgs &a, int storage, int threads, int smem_bytes, int cluster,
+                                  cudaStream_t stream);
+int cluster_smem_size(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap);
 
 // encode.cu
 cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, void *dst, int32_t d_pad,

@@ -64,11 +64,12 @@ class Index:
     @staticmethod
     def params(mode="sync", M0=1, t=1, R_ratio=0.8, rerank=False, threads=0, hash_bits=0,
                persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None,
-               order=None):
+               order=None, cluster=0):
         return _abi.SearchParams(mode=_abi.MODE[mode], M0=M0, t=t, R_ratio=R_ratio, rerank=int(rerank),
                                  threads=threads, hash_bits=hash_bits, persistent=int(persistent),
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
-                                 M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order))
+                                 M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order),
+                                 cluster=cluster)
 
     def search(self, queries, k, L, M, *, out=None, stream=None, with_stats=False, stats=None, **kw):
         """queries: CUDA float32 nq x d. Returns (ids int64, dists float32[, stats int64 nq x 8]).
