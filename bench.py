@@ -295,17 +295,19 @@ def run_ours(args):
         if args.skip_single or ("plain_f32", tgt) not in points:
             continue
         L, M = points[("plain_f32", tgt)]
-        lat = []
-        for i in range(300):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ix32.search(q[i:i + 1], K, L, M, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            lat.append(e0.elapsed_time(e1) * 1e3)
-        single[tgt] = {"L": L, "M": M, "p50_us": float(np.percentile(lat, 50)),
-                       "p99_us": float(np.percentile(lat, 99)), "qps": 1e6 / float(np.mean(lat))}
+        for C in (1, 4, 8):  # one CTA, or a cluster of C CTAs per query
+            lat = []
+            for i in range(300):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ix32.search(q[i:i + 1], K, L, M, stream=stream, cluster=C)
+                e1.record(stream)
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1) * 1e3)
+            single[f"{tgt}/cluster{C}"] = {"L": L, "M": M, "p50_us": float(np.percentile(lat, 50)),
+                                           "p99_us": float(np.percentile(lat, 99)),
+                                           "qps": 1e6 / float(np.mean(lat))}
 
     # ---- end to end through the host-buffer C call (H2D + search + D2H)
     L, M = points[head]
