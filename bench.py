@@ -281,6 +281,7 @@ def run_ours(args):
             row_bytes = ix.info()["d_pad"] * es
             b = algorithmic_bytes(st, w.R, row_bytes, w.d, K, L if kw.get("rerank") else 0)
             results[(name, tgt)] = {
+                "launch": ix.describe(nq, K, L, M, **kw),
                 "L": L, "M": M, "recall": recall_at_k(ids, gt), "ms_per_step": t * 1e3,
                 "qps": nq * world / t, "p50_us": float(np.percentile(svc, 50)),
                 "p99_us": float(np.percentile(svc, 99)), "alg_bytes": b, "gbs": b / t / 1e9,
@@ -357,8 +358,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": h["gbs"], "peak": hbm, "unit": "GB/s",
                      "frac": h["gbs"] / hbm, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "traffic": None,
-                     "kernel": f"sync_search_kernel<{256 if h['M'] * w.R >= 256 else 128}, "
-                               f"{'BF16' if head[0].startswith('batched') else 'F32'}>",
+                     "kernel": f"sync_search_kernel<{h['launch']['threads']}, "
+                               f"{'BF16' if head[0].startswith('batched') else 'F32'}>, grid {h['launch']['grid']}, "
+                               f"{h['launch']['smem_bytes']} B shared, 2^{h['launch']['hash_bits']} visited slots",
                      "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 (re-rank) + d*4 + k*12"},
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * w.d * 4,
                 "d2h_bytes_per_step": nq * K * 12},
@@ -404,9 +406,9 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     calib = w.queries[:200]
     gt, _ = oracle.exact_knn(w.base, calib, K, nthreads=cores)
-    L, M = 512, 4
+    L, M = 2048, 32  # the M of the GPU arm's recall-0.99 point; L calibrated on the sample
     for Lc in L_SWEEP:
-        ids, _, _ = oracle.search(w.base, w.adj, w.entry, calib, algo="topm", L=Lc, K=K, M0=1, M_max=4, t=1,
+        ids, _, _ = oracle.search(w.base, w.adj, w.entry, calib, algo="topm", L=Lc, K=K, M0=1, M_max=M, t=1,
                                   nthreads=cores)
         if recall_at_k(ids, gt) >= 0.99:
             L = Lc

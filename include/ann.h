@@ -162,6 +162,20 @@ int ann_search_ex(const ann_index *index, const float *queries, int64_t nq, int3
                   int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
                   void *stream);
 
+/* Launch configuration ann_search_ex would use for these arguments,
+ * without launching anything (argument errors as in ann_search_ex). */
+typedef struct {
+    int32_t threads;      /* threads per CTA */
+    int32_t smem_bytes;   /* dynamic shared memory per CTA */
+    int32_t grid;         /* CTAs launched */
+    int32_t hash_bits;    /* log2 slots of the visited table */
+    int32_t cluster;      /* CTAs per query */
+    int32_t mode;         /* ann_mode */
+} ann_launch_info;
+
+int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L, int32_t M,
+                        const ann_search_params *params, ann_launch_info *out);
+
 /* The same search from HOST buffers: copies the queries to the device,
  * searches, copies the results back and synchronises the stream before it
  * returns. queries host nq x d float32; out_ids / out_dists host nq x k.

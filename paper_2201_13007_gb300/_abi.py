@@ -69,6 +69,11 @@ class Result(ctypes.Structure):
                 ("device_start_ns", ctypes.c_int64), ("device_end_ns", ctypes.c_int64)]
 
 
+class LaunchInfo(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("hash_bits", ctypes.c_int32), ("cluster", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -94,6 +99,8 @@ def lib():
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp,
                                                   ctypes.POINTER(SearchParams), vp]
+            L.ann_search_describe.argtypes = [vp, i64, i32, i32, i32, ctypes.POINTER(SearchParams),
+                                              ctypes.POINTER(LaunchInfo)]
             L.ann_batch_create.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(BucketConfig), i32,
                                            ctypes.POINTER(SearchParams), ctypes.POINTER(vp)]
             L.ann_batch_search.argtypes = [vp, vp, vp, vp, vp]
@@ -203,3 +210,10 @@ def ann_batch_info(batch):
 
 def ann_batch_destroy(batch) -> None:
     lib().ann_batch_destroy(batch)
+
+
+def ann_search_describe(index, nq, k, L, M, params) -> dict:
+    out = LaunchInfo()
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().ann_search_describe(index, nq, k, L, M, p, ctypes.byref(out)))
+    return {f: getattr(out, f) for f, _ in LaunchInfo._fields_}

@@ -390,6 +390,22 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
     return ANN_OK;
 }
 
+int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L, int32_t M,
+                        const ann_search_params *params, ann_launch_info *out) {
+    if (!out) return fail(ANN_ERR_ARG, "out is NULL");
+    Plan plan;
+    int rc = plan_search(index, reinterpret_cast<const float *>(16), nq, k, L, M, reinterpret_cast<int64_t *>(16),
+                         reinterpret_cast<float *>(16), params, &plan);
+    if (rc != ANN_OK) return rc;
+    out->threads = plan.threads;
+    out->smem_bytes = plan.smem;
+    out->grid = plan.cluster > 1 ? (int32_t)(nq * plan.cluster) : plan.grid;
+    out->hash_bits = plan.a.hash_bits;
+    out->cluster = plan.cluster;
+    out->mode = plan.mode;
+    return ANN_OK;
+}
+
 const char *ann_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

@@ -71,6 +71,10 @@ class Index:
                                  M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order),
                                  cluster=cluster)
 
+    def describe(self, nq, k, L, M, **kw):
+        """Launch configuration of a search with these arguments (ann_search_describe)."""
+        return _abi.ann_search_describe(self.handle, nq, k, L, M, self.params(**kw))
+
     def search(self, queries, k, L, M, *, out=None, stream=None, with_stats=False, stats=None, **kw):
         """queries: CUDA float32 nq x d. Returns (ids int64, dists float32[, stats int64 nq x 8]).
         ``stats`` may be a preallocated CUDA int64 nq x 8 tensor for the per-query counters."""
