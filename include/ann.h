@@ -119,6 +119,13 @@ typedef struct {
      * shared memory (lower latency per query); 0 or 1 = one CTA per query.
      * A clustered search is never persistent (one cluster per query). */
     int32_t cluster;
+    /* Sync one-CTA kernel only: device int64 array of nq x 4, or NULL. When
+     * given, each query's SM clock cycles spent in its step phases are
+     * written there: [0] select (first M unchecked), [1] expand (adjacency
+     * rows + visited table), [2] distance gather, [3] sort + dedupe + merge.
+     * These are the Expand / Merge / Seq parts of the paper's time
+     * breakdown (Fig. 14). */
+    int64_t *phase_cycles;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

@@ -242,6 +242,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.work_counter = x.work_counter;
     a.persistent = p->persistent ? 1 : 0;
     a.order = p->order;
+    a.phase_cycles = reinterpret_cast<long long *>(p->phase_cycles);
     a.Lcap = L;
     int need = M * x.R;
     if (a.rerank && L > need) need = L;

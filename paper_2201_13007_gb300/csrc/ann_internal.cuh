@@ -61,6 +61,7 @@ struct SearchArgs {
     int *work_counter;
     int32_t persistent;
     const int32_t *order;  // work list: item i is query order[i] (nullptr: item i is query i)
+    long long *phase_cycles; // nq x 4 SM cycles per phase (select, expand, distance, sort+merge) or nullptr
     // shared-memory layout
     int32_t Lcap;        // queue capacity
     int32_t Ccap;        // candidate / sort buffer, power of two >= 32

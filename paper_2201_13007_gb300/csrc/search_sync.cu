@@ -39,6 +39,7 @@ struct Ctrl {
     int qi;
     // per-query counters, updated by thread 0 only
     long long steps, expansions, evals, resets, dropped, t0;
+    long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
 };
 
 template <int NT, int STORE>
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
             ctl.evals = 1;
             ctl.unsafe = 0;
+            ctl.ph[0] = ctl.ph[1] = ctl.ph[2] = ctl.ph[3] = 0;
         }
         __syncthreads();
         const int qi = ctl.qi;
@@ -110,6 +112,14 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
         int step = 0;
         entry_t *Q = Qa, *Qn = Qb;
+        const bool prof = a.phase_cycles != nullptr;
+        if (prof && tid == 0) ctl.tmark = clock64();
+#define ANN_PHASE(i)                                   \
+    if (prof && tid == 0) {                            \
+        const long long now_ = clock64();              \
+        ctl.ph[i] += now_ - ctl.tmark;                 \
+        ctl.tmark = now_;                              \
+    }
         for (;;) {
             int qlen = ctl.qlen;
             // --- forget the visited table when half full (keep the queued ids)
@@ -146,6 +156,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 }
             }
             __syncthreads();
+            ANN_PHASE(0)
             const int nact = ctl.nact;
             if (nact == 0) break;  // no unchecked vertex left
             step++;
@@ -173,6 +184,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 if (fresh) cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
             }
             __syncthreads();
+            ANN_PHASE(1)
             const int nc = ctl.ncand;
             if (tid == 0) {
                 ctl.hash_count += nc;
@@ -183,6 +195,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
                 compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
                 __syncthreads();
+                ANN_PHASE(2)
                 const int ns = ctl.ns;
                 if (ns > 0) {
                     // --- sort the survivors by (key, id)
@@ -251,8 +264,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 }
             }
             __syncthreads();
+            ANN_PHASE(3)
             if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
         }
+#undef ANN_PHASE
 
         // --- output: first k of the queue, optionally re-ranked with FP32 rows
         const int qlen = ctl.qlen;
@@ -291,6 +306,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             st.t_end_ns = global_ns();
             a.stats[qi] = st;
         }
+        if (tid == 0 && prof)
+            for (int i = 0; i < 4; ++i) a.phase_cycles[(size_t)qi * 4 + i] = ctl.ph[i];
         if (!a.persistent) break;
         __syncthreads();
     }
