@@ -236,6 +236,10 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.R_ratio = p->R_ratio;
     a.rerank = p->rerank ? 1 : 0;
     a.hash_bits = hb;
+    if (p->visited_mode < 0 || p->visited_mode > 1) return fail(ANN_ERR_ARG, "visited_mode=%d not 0 or 1", p->visited_mode);
+    if (p->visited_mode == 1 && (async || csize > 1))
+        return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
+    a.visited_mode = p->visited_mode;
     a.out_ids = out_ids;
     a.out_dists = out_dists;
     a.stats = p->stats;

@@ -55,6 +55,7 @@ struct SearchArgs {
     float R_ratio;
     int32_t rerank;
     int32_t hash_bits;
+    int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
     int64_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;

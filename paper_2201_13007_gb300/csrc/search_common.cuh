@@ -213,6 +213,17 @@ __device__ __forceinline__ int visited_insert(uint32_t *table, int bits, uint32_
     return 2;
 }
 
+// Direct-mapped visited cache: slot = hash(id); an insert exchanges the slot
+// with id. Returns 0 if the slot already held id (visited), 1 if the slot was
+// empty, 3 if another id was evicted (that id is now forgotten: it may be
+// evaluated again, and the merge must drop ids already queued).
+__device__ __forceinline__ int visited_exchange(uint32_t *table, int bits, uint32_t id) {
+    const uint32_t h = (id * 0x9E3779B1u) >> (32 - bits);
+    const uint32_t old = atomicExch(table + h, id);
+    if (old == id) return 0;
+    return old == kEmptySlot ? 1 : 3;
+}
+
 // ------------------------------------------------------------ bitonic sort
 __device__ __forceinline__ entry_t cmpx(entry_t v, int j, int k, int i) {
     entry_t p = __shfl_xor_sync(kFull, v, j);

@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     }
         for (;;) {
             int qlen = ctl.qlen;
-            // --- forget the visited table when half full (keep the queued ids)
-            if (ctl.hash_count * 2 > H) {
+            // --- forget the visited table when half full (keep the queued ids);
+            // the direct-mapped cache never resets, it forgets by eviction
+            if (a.visited_mode == 0 && ctl.hash_count * 2 > H) {
                 for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
                 __syncthreads();
                 for (int i = tid; i < qlen; i += NT) visited_insert(table, a.hash_bits, entry_id(Q[i]));
@@ -174,8 +175,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     const int aidx = i / R, r = i - aidx * R;
                     u = __ldg(a.adj + (size_t)act[aidx] * R + r);
                 }
-                const int ins = u >= 0 ? visited_insert(table, a.hash_bits, (uint32_t)u) : 0;
-                if (ins == 2) ctl.unsafe = 1;  // probe limit hit: this vertex may be a repeat
+                int ins = 0;
+                if (u >= 0)
+                    ins = a.visited_mode == 0 ? visited_insert(table, a.hash_bits, (uint32_t)u)
+                                              : visited_exchange(table, a.hash_bits, (uint32_t)u);
+                if (ins >= 2) ctl.unsafe = 1;  // a vertex may have been forgotten: repeats possible
                 const bool fresh = ins != 0;
                 const unsigned bal = __ballot_sync(kFull, fresh);
                 int basepos = 0;

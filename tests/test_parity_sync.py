@@ -233,3 +233,17 @@ def test_reduced_precision_with_rerank(ann, oracle_mod, storage):
     compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
                   np.zeros(clean.sum()), w.base, w.queries[clean], "l2")
     ix.close()
+
+
+@pytest.mark.parametrize("hash_bits", [8, 10, 12])
+def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash_bits):
+    """The direct-mapped visited cache forgets a vertex whenever another one
+    hashes to its slot; ids and keys must still be exact (reading 14)."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=1)
+    o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
+                                            M0=1, M_max=8, t=1, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+    s = stats_dict(st)
+    assert (s["evals"] >= o_st["evals"]).all()
