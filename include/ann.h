@@ -132,6 +132,13 @@ typedef struct {
      * its slot. Both only ever forget, which changes the number of distance
      * evaluations but never the results. */
     int32_t visited_mode;
+    /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: shared memory for
+     * staging candidate rows with bulk copies (one cp.async.bulk per row,
+     * completing on an mbarrier), instead of gathering them through
+     * registers; 0 or -1 = register gather. A query whose copies do not
+     * arrive within the kernel's wait limit gets (-1, +inf) results and
+     * stats.steps = -2. */
+    int32_t stage_bytes;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

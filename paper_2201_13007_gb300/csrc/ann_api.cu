@@ -240,6 +240,12 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (p->visited_mode == 1 && (async || csize > 1))
         return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
     a.visited_mode = p->visited_mode;
+    if (p->stage_bytes < -1) return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
+    if (p->stage_bytes > 0 && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
+        const int row_bytes = x.d_pad * ann::storage_bytes(x.storage);
+        a.tma_rows = p->stage_bytes / row_bytes;
+        if (a.tma_rows < 1) a.tma_rows = 1;
+    }
     a.out_ids = out_ids;
     a.out_dists = out_dists;
     a.stats = p->stats;
@@ -255,7 +261,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     auto smem_for = [&](int bits) {
         if (csize > 1) return ann::cluster_smem_size(a.qfloats, a.Lcap, a.Ccap, bits, M);
         return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
-                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M).total;
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M,
+                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage)).total;
     };
     int smem = smem_for(a.hash_bits);
     // an automatic visited table shrinks until the layout fits (it may then forget more often)

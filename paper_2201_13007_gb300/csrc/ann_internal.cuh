@@ -56,6 +56,7 @@ struct SearchArgs {
     int32_t rerank;
     int32_t hash_bits;
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
+    int32_t tma_rows;      // rows per bulk-copy staging batch (0 = gather rows through registers)
     int64_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;
@@ -71,12 +72,13 @@ struct SearchArgs {
 
 // Byte offsets of the dynamic shared-memory segments (16-byte aligned).
 struct SmemLayout {
-    int q_off, q0_off, q1_off, cand_off, cand2_off, dup_off, hash_off, act_off, total;
+    int q_off, q0_off, q1_off, cand_off, cand2_off, dup_off, hash_off, act_off, bar_off, stage_off, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap) {
+__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
+                                                  int stage_bytes = 0) {
     SmemLayout s;
     int o = 0;
     s.q_off = o;    o += align16(qfloats * 4);
@@ -87,6 +89,8 @@ __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Cca
     s.dup_off = o;  o += align16(Ccap);
     s.hash_off = o; o += align16((1 << hash_bits) * 4);
     s.act_off = o;  o += align16(Mcap * 4);
+    s.bar_off = o;  o += 16;
+    s.stage_off = o; o += align16(stage_bytes);
     s.total = o;
     return s;
 }

@@ -416,3 +416,108 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
 namespace ann {
 
 }  // namespace ann
+
+namespace ann {
+
+// ------------------------------------------------------------- TMA staging
+// One-dimensional bulk copies (cp.async.bulk) of whole rows into shared
+// memory, completing on an mbarrier with a transaction count. A copy moves a
+// row with a single instruction and holds no registers while in flight, so a
+// CTA can keep as many rows in flight as its staging area holds.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on the phase with the given parity; returns false if the
+// phase did not complete within the iteration limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int max_iters) {
+    for (int i = 0; i < max_iters; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_row_to_smem(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Keys of the nc candidates in cand[] (ids in the low word), rows fetched by
+// bulk copies in batches of up to stage_rows rows; survivors below `limit`
+// are appended to out[] through *out_n (as compute_keys does). *parity is the
+// mbarrier phase to wait for next and is advanced per batch. Returns false
+// (identically in every thread) if a batch did not arrive within the wait
+// limit. Every thread must call it; it ends with a __syncthreads().
+template <int STORE, int NT>
+__device__ bool compute_keys_tma(const void *rows, int row_elems, int metric, const float *qv, const entry_t *cand,
+                                 int nc, unsigned char *stage, int stage_rows, unsigned long long *bar,
+                                 unsigned *parity, entry_t limit, entry_t *out, int *out_n) {
+    constexpr int NW = NT / 32;
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpr = row_elems / EPC;
+    const int row_bytes = cpr * 16;
+    int ts = 1;
+    while (ts < cpr && ts < 32) ts <<= 1;
+    const int rpw = 32 / ts;
+    const int team = lane / ts, tl = lane & (ts - 1);
+    const int iters = (cpr + ts - 1) / ts;
+    const bool l2 = metric == ANN_METRIC_L2;
+    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
+    for (int b0 = 0; b0 < nc; b0 += stage_rows) {
+        const int nb = min(stage_rows, nc - b0);
+        if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(nb * row_bytes));
+        __syncthreads();
+        for (int r = tid; r < nb; r += NT) {
+            const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
+            bulk_row_to_smem(stage + (size_t)r * row_bytes, g + (size_t)id * row_bytes, (unsigned)row_bytes, bar);
+        }
+        const bool ok = mbar_wait(bar, *parity, 1 << 22);
+        *parity ^= 1u;
+        if (__syncthreads_or(!ok)) return false;
+        for (int c0 = warp * rpw; c0 < nb; c0 += NW * rpw) {
+            const int r = c0 + team;
+            const bool valid = r < nb;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int it = 0; it < iters; ++it) {
+                const int ch = tl + it * ts;
+                if (valid && ch < cpr) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(stage + (size_t)r * row_bytes + ch * 16);
+                    Chunk<STORE>::add(acc, v, qv + ch * EPC, 1.f, l2);
+                }
+            }
+            float s = acc.x + acc.y;
+            for (int off = ts >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+            const uint32_t id = valid ? (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull) : 0u;
+            const entry_t e = pack_entry(l2 ? s : -s, id);
+            const bool keep = tl == 0 && valid && e < limit;
+            const unsigned bal = __ballot_sync(kFull, keep);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+            base = __shfl_sync(kFull, base, 0);
+            if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
+        }
+        __syncthreads();
+        fence_proxy_async_smem();  // the stage's generic reads finish before the next bulk writes
+    }
+    return true;
+}
+
+}  // namespace ann

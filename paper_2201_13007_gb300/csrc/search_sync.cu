@@ -47,7 +47,15 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M);
+    const int row_bytes = a.d_pad * (STORE == ANN_STORE_F32 ? 4 : STORE == ANN_STORE_E4M3 ? 1 : 2);
+    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, a.tma_rows * row_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + lay.bar_off);
+    unsigned char *stage = smem + lay.stage_off;
+    unsigned parity = 0;
+    if (a.tma_rows > 0) {
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+    }
     float *qv = reinterpret_cast<float *>(smem + lay.q_off);
     entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
     entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
@@ -197,8 +205,26 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             if (nc > 0) {
                 // --- distances; only candidates below the L-th queued entry survive
                 const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
-                compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
-                __syncthreads();
+                if (STORE != ANN_STORE_E4M3 && a.tma_rows > 0) {
+                    if (!compute_keys_tma<STORE, NT>(a.base, a.d_pad, a.metric, qv, cand, nc, stage, a.tma_rows, bar,
+                                                     &parity, limit, surv, &ctl.ns)) {
+                        // a staging batch never arrived: fail this query, let the copies land, stop
+                        mbar_wait(bar, parity ^ 1u, 1 << 22);
+                        for (int i = tid; i < a.k; i += NT) {
+                            a.out_ids[(size_t)qi * a.k + i] = -1;
+                            a.out_dists[(size_t)qi * a.k + i] = __int_as_float(0x7f800000);
+                        }
+                        if (tid == 0 && a.stats) {
+                            ann_query_stats st = {};
+                            st.steps = -2;
+                            a.stats[qi] = st;
+                        }
+                        return;
+                    }
+                } else {
+                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
+                    __syncthreads();
+                }
                 ANN_PHASE(2)
                 const int ns = ctl.ns;
                 if (ns > 0) {

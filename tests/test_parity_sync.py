@@ -247,3 +247,19 @@ def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash
     compare_exact(ids, dists, o_ids, o_keys)
     s = stats_dict(st)
     assert (s["evals"] >= o_st["evals"]).all()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("stage_bytes", [1, 8192, 65536])
+def test_bulk_copy_staging_exact(ann, oracle_mod, sift_small, storage, stage_bytes):
+    """Rows staged by cp.async.bulk into shared memory (one row per copy,
+    completing on an mbarrier) give exactly the register-gather answers;
+    integer data, so also exactly the oracle's (FP16 holds 0..255 exactly)."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    for L, M in ((64, 4), (200, 16)):
+        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, stage_bytes=stage_bytes)
+        o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
+                                                M0=1, M_max=M, t=1, nthreads=8)
+        compare_exact(ids, dists, o_ids, o_keys)
+        np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
