@@ -119,10 +119,6 @@ template <> struct Chunk<ANN_STORE_E4M3> {
     }
 };
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ uint4 ld_row_chunk(const uint4 *p) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -142,8 +138,7 @@ template <int STORE, int NT, int U = 2>
 __device__ __forceinline__ void compute_keys(const void *rows, const float *scales, int row_elems,
                                              int metric, const float *qv, entry_t *cand, int nc,
                                              entry_t limit = kEmptyEntry, entry_t *out = nullptr,
-                                             int *out_n = nullptr, const int32_t *prefetch_adj = nullptr,
-                                             int prefetch_R = 0) {
+                                             int *out_n = nullptr) {
     constexpr int NW = NT / 32;
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,11 +188,7 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
                 int base = 0;
                 if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
                 base = __shfl_sync(kFull, base, 0);
-                if (keep) {
-                    out[base + __popc(bal & ((1u << lane) - 1u))] = e;
-                    // a survivor may be expanded next step: bring its adjacency row into L2 now
-                    if (prefetch_adj) prefetch_l2(prefetch_adj + (size_t)id[u] * prefetch_R);
-                }
+                if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
             }
         }
     }

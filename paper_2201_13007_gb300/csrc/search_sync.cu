@@ -246,8 +246,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                         return;
                     }
                 } else {
-                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns,
-                                            a.adj, R);
+                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
                     __syncthreads();
                 }
                 ANN_PHASE(2)
