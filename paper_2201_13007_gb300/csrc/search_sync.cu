@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     unsigned char *dup = smem + lay.dup_off;
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
     int *act = reinterpret_cast<int *>(smem + lay.act_off);
-    __shared__ int chunk_cnt[64];  // unchecked entries per 32-entry chunk of the queue (L <= 2048)
     const int H = 1 << a.hash_bits;
     const int R = a.R;
 
@@ -143,49 +142,26 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     ctl.unsafe = 1;
                 }
             }
-            // --- select the first Mcur unchecked entries (rank order) and mark them:
-            // every warp counts the unchecked entries of its 32-entry chunks, a
-            // prefix over the chunk counts gives each chunk its first pick
-            const int nchunks = (qlen + 31) >> 5;
-            for (int c = warp; c < nchunks; c += NT / 32) {
-                const int i = c * 32 + lane;
-                const bool un = i < qlen && !(Q[i] & kChecked);
-                const unsigned bal = __ballot_sync(kFull, un);
-                if (lane == 0) chunk_cnt[c] = __popc(bal);
-            }
-            __syncthreads();
+            // --- select the first Mcur unchecked entries (rank order) and mark them
             if (warp == 0) {
-                int run = 0;
-                for (int c0 = 0; c0 < nchunks; c0 += 32) {
-                    const int c = c0 + lane;
-                    const int v = c < nchunks ? chunk_cnt[c] : 0;
-                    int incl = v;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += t;
+                int found = 0;
+                for (int b = 0; b < qlen && found < Mcur; b += 32) {
+                    const int i = b + lane;
+                    entry_t e = i < qlen ? Q[i] : kChecked;
+                    const bool un = !(e & kChecked);
+                    const unsigned bal = __ballot_sync(kFull, un);
+                    const int r = found + __popc(bal & ((1u << lane) - 1u));
+                    if (un && r < Mcur) {
+                        act[r] = (int)entry_id(e);
+                        Q[i] = e | kChecked;
                     }
-                    if (c < nchunks) chunk_cnt[c] = run + incl - v;  // exclusive prefix
-                    run += __shfl_sync(kFull, incl, 31);
+                    found += __popc(bal);
                 }
                 if (lane == 0) {
-                    ctl.nact = run < Mcur ? run : Mcur;
+                    ctl.nact = found < Mcur ? found : Mcur;
                     ctl.ncand = 0;
                     ctl.anydup = 0;
                     ctl.ns = 0;
-                }
-            }
-            __syncthreads();
-            for (int c = warp; c < nchunks; c += NT / 32) {
-                const int pre = chunk_cnt[c];
-                if (pre >= Mcur) continue;  // warp-uniform
-                const int i = c * 32 + lane;
-                const entry_t e = i < qlen ? Q[i] : kChecked;
-                const bool un = !(e & kChecked);
-                const unsigned bal = __ballot_sync(kFull, un);
-                const int r = pre + __popc(bal & ((1u << lane) - 1u));
-                if (un && r < Mcur) {
-                    act[r] = (int)entry_id(e);
-                    Q[i] = e | kChecked;
                 }
             }
             __syncthreads();
