@@ -157,6 +157,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(torch, dist, seconds, device="cuda"):
+    """The slowest rank's time (every rank gets the same value)."""
+    if dist is None:
+        return seconds
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algorithmic_bytes(stats, R, row_bytes, d, k, rerank_rows):
     """Bytes the method must move per step: adjacency rows of every expanded
     vertex, a stored row per distance, the FP32 rows re-ranked, the query and
@@ -272,11 +281,7 @@ def run_ours(args):
         for (name, tgt), (L, M) in points.items():
             ix, kw, es = forms[name]
             times, ids, st = timed(ix, kw, L, M, args.steps, args.warmup)
-            t = float(np.mean(times))
-            if dist is not None:
-                tt = torch.tensor([t], device="cuda")
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                t = float(tt.item())
+            t = max_over_ranks(torch, dist, float(np.mean(times)))
             svc = (st[:, 7] - st[:, 6]) / 1e3
             row_bytes = ix.info()["d_pad"] * es
             b = algorithmic_bytes(st, w.R, row_bytes, w.d, K, L if kw.get("rerank") else 0)
@@ -326,11 +331,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         ix.search_host(hq, K, L, M, out=(hids, hd), **kw)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(torch, dist, float(np.mean(e2e_t)) if e2e_t else float("nan"))
 
     # ---- CPU baseline: the oracle as it stands, bounded sample, rank 0 at N = 1
     cpu = None
