@@ -139,6 +139,11 @@ typedef struct {
      * arrive within the kernel's wait limit gets (-1, +inf) results and
      * stats.steps = -2. */
     int32_t stage_bytes;
+    /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: 1 = each lane streams
+     * the row chunks it reduces through a private shared-memory ring with
+     * cp.async, four groups ahead (more rows in flight per warp, no
+     * barriers); 0 = register gather. */
+    int32_t lane_pipeline;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

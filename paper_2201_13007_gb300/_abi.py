@@ -51,7 +51,8 @@ class SearchParams(ctypes.Structure):
                 ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
                 ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p),
                 ("order", ctypes.c_void_p), ("cluster", ctypes.c_int32), ("phase_cycles", ctypes.c_void_p),
-                ("visited_mode", ctypes.c_int32), ("stage_bytes", ctypes.c_int32)]
+                ("visited_mode", ctypes.c_int32), ("stage_bytes", ctypes.c_int32),
+                ("lane_pipeline", ctypes.c_int32)]
 
 
 class BucketConfig(ctypes.Structure):

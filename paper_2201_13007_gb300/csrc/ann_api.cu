@@ -241,7 +241,14 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
     a.visited_mode = p->visited_mode;
     if (p->stage_bytes < -1) return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
-    if (p->stage_bytes > 0 && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
+    if (p->lane_pipeline && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
+        // per lane: 4 groups of 2 rows of its team in flight (compute_keys_pipe<.., U = 2, D = 4>)
+        const int es = ann::storage_bytes(x.storage);
+        const int cpr = x.d_pad * es / 16;
+        int ts = 1;
+        while (ts < cpr && ts < 32) ts <<= 1;
+        a.pipe_bytes = (threads / 32) * 4 * 2 * (32 / ts) * x.d_pad * es;
+    } else if (p->stage_bytes > 0 && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
         const int row_bytes = x.d_pad * ann::storage_bytes(x.storage);
         a.tma_rows = p->stage_bytes / row_bytes;
         if (a.tma_rows < 1) a.tma_rows = 1;
@@ -262,7 +269,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         if (csize > 1) return ann::cluster_smem_size(a.qfloats, a.Lcap, a.Ccap, bits, M);
         return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
                      : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M,
-                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage)).total;
+                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage) + a.pipe_bytes).total;
     };
     int smem = smem_for(a.hash_bits);
     // an automatic visited table shrinks until the layout fits (it may then forget more often)

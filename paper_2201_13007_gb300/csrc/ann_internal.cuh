@@ -57,6 +57,7 @@ struct SearchArgs {
     int32_t hash_bits;
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
     int32_t tma_rows;      // rows per bulk-copy staging batch (0 = gather rows through registers)
+    int32_t pipe_bytes;    // per-CTA ring of the per-lane cp.async pipeline (0 = off)
     int64_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;

@@ -521,3 +521,98 @@ __device__ bool compute_keys_tma(const void *rows, int row_elems, int metric, co
 }
 
 }  // namespace ann
+
+namespace ann {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// compute_keys (filtered form) with each lane's row chunks streamed through
+// a private shared-memory ring by cp.async: a lane copies exactly the chunks
+// it later reduces, D groups of U rows per team ahead, so rows stay in flight
+// without holding registers and without any barrier between lanes or warps.
+// ring: this CTA's staging area, (NT/32) * D * U * rpw * row_bytes bytes.
+template <int STORE, int NT, int U = 2, int D = 4>
+__device__ __forceinline__ void compute_keys_pipe(const void *rows, const float *scales, int row_elems, int metric,
+                                                  const float *qv, const entry_t *cand, int nc, unsigned char *ring,
+                                                  entry_t limit, entry_t *out, int *out_n) {
+    constexpr int NW = NT / 32;
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cpr = row_elems / EPC;
+    const int row_bytes = cpr * 16;
+    int ts = 1;
+    while (ts < cpr && ts < 32) ts <<= 1;
+    const int rpw = 32 / ts;
+    const int team = lane / ts, tl = lane & (ts - 1);
+    const int iters = (cpr + ts - 1) / ts;
+    const bool l2 = metric == ANN_METRIC_L2;
+    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
+    unsigned char *wring = ring + (size_t)warp * D * U * rpw * row_bytes;
+    const int per = NW * rpw * U;                 // rows per group over the whole CTA
+    const int first = warp * rpw * U;
+    const int ngroups = first < nc ? (nc - first + per - 1) / per : 0;  // warp-uniform
+    auto slot = [&](int k, int u) { return wring + ((size_t)((k % D) * U + u) * rpw + team) * row_bytes; };
+    auto issue = [&](int k) {
+        if (k < ngroups) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = first + k * per + u * rpw + team;
+                if (c < nc) {
+                    const uint32_t id = (uint32_t)(cand[c] & 0xFFFFFFFFull);
+                    const unsigned char *src = g + (size_t)id * row_bytes;
+                    unsigned char *dst = slot(k, u);
+                    for (int it = 0; it < iters; ++it) {
+                        const int ch = tl + it * ts;
+                        if (ch < cpr) cp_async16(dst + ch * 16, src + ch * 16);
+                    }
+                }
+            }
+        }
+        cp_async_commit();  // one group per step of the pipeline, possibly empty
+    };
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k) issue(k);
+    for (int k = 0; k < ngroups; ++k) {
+        issue(k + D - 1);
+        cp_async_wait<D - 1>();  // this lane's copies of group k have landed
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = first + k * per + u * rpw + team;
+            const bool valid = c < nc;
+            float2 acc = make_float2(0.f, 0.f);
+            uint32_t id = 0;
+            float sc = 1.f;
+            if (valid) {
+                id = (uint32_t)(cand[c] & 0xFFFFFFFFull);
+                if (STORE == ANN_STORE_E4M3) sc = __ldg(scales + id);
+                const unsigned char *src = slot(k, u);
+                for (int it = 0; it < iters; ++it) {
+                    const int ch = tl + it * ts;
+                    if (ch < cpr) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(src + ch * 16);
+                        Chunk<STORE>::add(acc, v, qv + ch * EPC, sc, l2);
+                    }
+                }
+            }
+            float s = acc.x + acc.y;
+            for (int off = ts >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+            const entry_t e = pack_entry(l2 ? s : -s, id);
+            const bool keep = tl == 0 && valid && e < limit;
+            const unsigned bal = __ballot_sync(kFull, keep);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+            base = __shfl_sync(kFull, base, 0);
+            if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace ann

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row_bytes = a.d_pad * (STORE == ANN_STORE_F32 ? 4 : STORE == ANN_STORE_E4M3 ? 1 : 2);
-    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, a.tma_rows * row_bytes);
+    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M,
+                                       a.tma_rows * row_bytes + a.pipe_bytes);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + lay.bar_off);
     unsigned char *stage = smem + lay.stage_off;
     unsigned parity = 0;
@@ -221,6 +222,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                         }
                         return;
                     }
+                } else if (STORE != ANN_STORE_E4M3 && a.pipe_bytes > 0) {
+                    compute_keys_pipe<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, stage, limit, surv,
+                                                 &ctl.ns);
+                    __syncthreads();
                 } else {
                     compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
                     __syncthreads();

@@ -263,3 +263,18 @@ def test_bulk_copy_staging_exact(ann, oracle_mod, sift_small, storage, stage_byt
                                                 M0=1, M_max=M, t=1, nthreads=8)
         compare_exact(ids, dists, o_ids, o_keys)
         np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("threads", [128, 512])
+def test_lane_pipeline_exact(ann, oracle_mod, sift_small, storage, threads):
+    """Rows streamed through each lane's cp.async ring give exactly the
+    oracle's answers (integer data)."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    for L, M in ((16, 1), (64, 4), (200, 16), (128, 32)):
+        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, lane_pipeline=1, threads=threads)
+        o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
+                                                M0=1, M_max=M, t=1, nthreads=8)
+        compare_exact(ids, dists, o_ids, o_keys)
+        np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
