@@ -126,11 +126,12 @@ typedef struct {
      * These are the Expand / Merge / Seq parts of the paper's time
      * breakdown (Fig. 14). */
     int64_t *phase_cycles;
-    /* Visited set of the one-CTA sync kernel: 0 = open-addressing table,
-     * exact until it is half full, then reset to the queued ids; 1 =
-     * direct-mapped cache that forgets a vertex when another one hashes to
-     * its slot. Both only ever forget, which changes the number of distance
-     * evaluations but never the results. */
+    /* Visited set: 1 = open-addressing table, exact until it is half full,
+     * then reset to the queued ids; 2 = direct-mapped cache that forgets a
+     * vertex when another one hashes to its slot (one-CTA sync kernel only);
+     * 0 = auto (2 for the one-CTA sync kernel, else 1). Both only ever
+     * forget, which changes the number of distance evaluations but never the
+     * results. */
     int32_t visited_mode;
     /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: shared memory for
      * staging candidate rows with bulk copies (one cp.async.bulk per row,

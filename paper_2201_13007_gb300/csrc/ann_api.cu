@@ -236,10 +236,12 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.R_ratio = p->R_ratio;
     a.rerank = p->rerank ? 1 : 0;
     a.hash_bits = hb;
-    if (p->visited_mode < 0 || p->visited_mode > 1) return fail(ANN_ERR_ARG, "visited_mode=%d not 0 or 1", p->visited_mode);
-    if (p->visited_mode == 1 && (async || csize > 1))
+    if (p->visited_mode < 0 || p->visited_mode > 2)
+        return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2}", p->visited_mode);
+    if (p->visited_mode == 2 && (async || csize > 1))
         return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
-    a.visited_mode = p->visited_mode;
+    // auto: the direct-mapped cache for the one-CTA sync kernel (measured 1-5 % faster), else open addressing
+    a.visited_mode = p->visited_mode == 0 ? ((async || csize > 1) ? 0 : 1) : p->visited_mode - 1;
     if (p->stage_bytes < -1) return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
     if (p->lane_pipeline && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
         // per lane: 4 groups of 2 rows of its team in flight (compute_keys_pipe<.., U = 2, D = 4>)

@@ -27,7 +27,7 @@ def test_cluster_equals_single_cta_and_oracle(env, oracle_mod, C, L, M):
     Index, w = env
     ix = Index(w.base, w.adj, w.entry)
     q = torch.from_numpy(w.queries).cuda()
-    a_ids, a_d, a_st = ix.search(q, 10, L, M, hash_bits=15, with_stats=True)
+    a_ids, a_d, a_st = ix.search(q, 10, L, M, hash_bits=15, visited_mode=1, with_stats=True)
     b_ids, b_d, b_st = ix.search(q, 10, L, M, hash_bits=15, cluster=C, with_stats=True)
     torch.cuda.synchronize()
     assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)

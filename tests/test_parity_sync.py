@@ -46,7 +46,7 @@ def test_tiny_float_parity(ann, oracle_mod, tiny, L, M):
     """Config: 10,000 x 32 FP32 mixture, exact 16-NN + reverse edges (cap 24),
     100 queries, k = 10, one CTA per query."""
     _, Index, stats_dict = ann
-    ids, dists, st = _run(Index, tiny, L=L, M=M, hash_bits=15)
+    ids, dists, st = _run(Index, tiny, L=L, M=M, hash_bits=15, visited_mode=1)
     o_ids, o_keys, o_st = oracle_mod.search(tiny.base, tiny.adj, tiny.entry, tiny.queries, algo="topm",
                                             L=L, K=10, M0=1, M_max=M, t=1, nthreads=8,
                                             tie_tol=fp32_tie_window(tiny.base, tiny.queries, "l2")[0])
@@ -67,7 +67,7 @@ def test_integer_data_bit_exact(ann, oracle_mod, sift_small, storage, L, M):
     must equal the oracle's bit for bit (BF16 holds 0..255 exactly)."""
     _, Index, stats_dict = ann
     w = sift_small
-    ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15)
+    ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, visited_mode=1)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
                                             M0=1, M_max=M, t=1, nthreads=8)
     compare_exact(ids, dists, o_ids, o_keys)
@@ -83,7 +83,7 @@ def test_forgetful_visited_table_keeps_ids(ann, oracle_mod, sift_small, hash_bit
     exact (the merge drops re-found queued ids), only evals grow."""
     _, Index, stats_dict = ann
     w = sift_small
-    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits)
+    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=1)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
                                             M0=1, M_max=8, t=1, nthreads=8)
     compare_exact(ids, dists, o_ids, o_keys)
@@ -241,7 +241,7 @@ def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash
     hashes to its slot; ids and keys must still be exact (reading 14)."""
     _, Index, stats_dict = ann
     w = sift_small
-    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=1)
+    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=2)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
                                             M0=1, M_max=8, t=1, nthreads=8)
     compare_exact(ids, dists, o_ids, o_keys)
@@ -258,7 +258,8 @@ def test_bulk_copy_staging_exact(ann, oracle_mod, sift_small, storage, stage_byt
     _, Index, stats_dict = ann
     w = sift_small
     for L, M in ((64, 4), (200, 16)):
-        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, stage_bytes=stage_bytes)
+        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, stage_bytes=stage_bytes,
+                              visited_mode=1)
         o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
                                                 M0=1, M_max=M, t=1, nthreads=8)
         compare_exact(ids, dists, o_ids, o_keys)
@@ -273,7 +274,8 @@ def test_lane_pipeline_exact(ann, oracle_mod, sift_small, storage, threads):
     _, Index, stats_dict = ann
     w = sift_small
     for L, M in ((16, 1), (64, 4), (200, 16), (128, 32)):
-        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, lane_pipeline=1, threads=threads)
+        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, lane_pipeline=1, threads=threads,
+                              visited_mode=1)
         o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
                                                 M0=1, M_max=M, t=1, nthreads=8)
         compare_exact(ids, dists, o_ids, o_keys)
