@@ -166,6 +166,23 @@ def max_over_ranks(torch, dist, seconds, device="cuda"):
     return float(t.item())
 
 
+def profiled_traffic(kernel_label):
+    """DRAM bytes per launch (read + write) from the committed ncu summary of
+    the headline kernel, if that summary was taken with this exact launch
+    configuration; else None."""
+    p = os.path.join(ROOT, "profiles", "sync_search_kernel_sift1m_L640_M32_bf16.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "traffic_config"):
+            k, v = line.split(":", 1)
+            vals[k] = v.strip()
+    if vals.get("traffic_config") != kernel_label or "traffic_bytes_per_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
+
+
 def algorithmic_bytes(stats, R, row_bytes, d, k, rerank_rows):
     """Bytes the method must move per step: adjacency rows of every expanded
     vertex, a stored row per distance, the FP32 rows re-ranked, the query and
@@ -344,6 +361,8 @@ def run_ours(args):
         return
     hbm, peak_kind = peaks()
     h = results[head]
+    klabel = (f"sync_search_kernel<{h['launch']['threads']}, {'BF16' if head[0].startswith('batched') else 'F32'}>, "
+              f"grid {h['launch']['grid']}, {h['launch']['smem_bytes']} B shared, 2^{h['launch']['hash_bits']} visited slots")
     out = {
         "metric": "QPS at recall@10>=0.99 (batched BF16 + FP32 re-rank, 1M x 128)",
         "value": h["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -358,10 +377,10 @@ def run_ours(args):
         "latency_kind": "per-query device service time (globaltimer, start to results written)",
         "roofline": {"bound": "hbm", "achieved": h["gbs"], "peak": hbm, "unit": "GB/s",
                      "frac": h["gbs"] / hbm, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                     "traffic": None,
-                     "kernel": f"sync_search_kernel<{h['launch']['threads']}, "
-                               f"{'BF16' if head[0].startswith('batched') else 'F32'}>, grid {h['launch']['grid']}, "
-                               f"{h['launch']['smem_bytes']} B shared, 2^{h['launch']['hash_bits']} visited slots",
+                     "traffic": profiled_traffic(klabel),
+                     "traffic_source": "profiles/sync_search_kernel_sift1m_L640_M32_bf16.md (one ncu capture, "
+                                       "dram__bytes_read.sum + dram__bytes_write.sum per launch)",
+                     "kernel": klabel,
                      "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 (re-rank) + d*4 + k*12"},
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * w.d * 4,
                 "d2h_bytes_per_step": nq * K * 12},
