@@ -312,6 +312,21 @@ def run_ours(args):
             }
     clocks = clk.summary()
 
+    # ---- the paper's asynchronous form (Algorithm 3 + Algorithm 2, R = 0.8), BF16 + FP32 re-rank,
+    # at the cheapest points of a sweep on this workload (one walker per warp)
+    async_pts = {}
+    if ix16 is not None and not args.point:
+        for tgt, (L, M) in ((0.9, (128, 4)), (0.99, (512, 8))):
+            kw = dict(mode="async", R_ratio=0.8, rerank=True, persistent=True)
+            st = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
+            ids, _ = ix16.search(q, K, L, M, stats=st, **kw)
+            times = event_time(torch, lambda: ix16.search(q, K, L, M, **kw), 3, 1, flush)
+            t = max_over_ranks(torch, dist, float(np.mean(times)))
+            sn = st.cpu().numpy()
+            async_pts[str(tgt)] = {"L": L, "M": M, "R": 0.8, "recall": recall_at_k(ids.cpu().numpy(), gt),
+                                   "qps": nq * world / t, "evals_per_query": float(sn[:, 2].mean()),
+                                   "merges_per_query": float(sn[:, 5].mean())}
+
     # ---- plain one query per launch (latency form) on a subset
     single = {}
     for tgt in TARGETS:
@@ -389,6 +404,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "points": {f"{nm}@{tgt}": v for (nm, tgt), v in results.items()},
         "one_query_per_launch": {str(k): v for k, v in single.items()},
+        "async_alg3_bf16_rerank": async_pts,
         "setup_s": setup_s,
     }
     print(json.dumps(out))

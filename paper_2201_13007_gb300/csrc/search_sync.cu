@@ -113,13 +113,13 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         if (tid == 0) {
             Qa[0] = cand[0];
             visited_insert(table, a.hash_bits, (uint32_t)a.entry);
-            ctl.qlen = 1;
             ctl.hash_count = 1;
         }
         __syncthreads();
 
         int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
         int step = 0;
+        int qlen = 1;  // the same in every thread
         entry_t *Q = Qa, *Qn = Qb;
         const bool prof = a.phase_cycles != nullptr;
         if (prof && tid == 0) ctl.tmark = clock64();
@@ -130,7 +130,6 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         ctl.tmark = now_;                              \
     }
         for (;;) {
-            int qlen = ctl.qlen;
             // --- forget the visited table when half full (keep the queued ids);
             // the direct-mapped cache never resets, it forgets by eviction
             if (a.visited_mode == 0 && ctl.hash_count * 2 > H) {
@@ -291,21 +290,19 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                         const int pos = j + count_below(Q, qlen, c);
                         if (pos < L) Qn[pos] = c;
                     }
-                    __syncthreads();
-                    if (tid == 0) ctl.qlen = min(L, qlen + ncl);
+                    __syncthreads();  // the new queue is complete; nothing of the old one is read again
+                    qlen = min(L, qlen + ncl);
                     entry_t *tmp = Q;
                     Q = Qn;
                     Qn = tmp;
                 }
             }
-            __syncthreads();
             ANN_PHASE(3)
             if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
         }
 #undef ANN_PHASE
 
         // --- output: first k of the queue, optionally re-ranked with FP32 rows
-        const int qlen = ctl.qlen;
         const entry_t *res = Q;
         if (a.rerank) {
             for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
