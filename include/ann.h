@@ -145,6 +145,23 @@ typedef struct {
      * cp.async, four groups ahead (more rows in flight per warp, no
      * barriers); 0 = register gather. */
     int32_t lane_pipeline;
+    /* Sync kernels: 1 = the row of every vertex that passes the visited
+     * filter is requested into L2 with one bulk prefetch
+     * (cp.async.bulk.prefetch.L2) the moment it passes, so all of a step's
+     * rows are in flight before the register gather reads them, and the
+     * final queue's FP32 rows are requested the same way before a re-rank;
+     * 2 = no prefetch; 0 = auto (1). Results never depend on it. */
+    int32_t l2_prefetch;
+    /* Sync kernels (one CTA or one cluster per query), distance gather:
+     * lanes that share one candidate row, a power of two from 1 to 32. Each
+     * lane streams its own 16-byte chunks of the row (two in flight) and the
+     * team adds its partial sums with log2(team_lanes) shuffles. -1 = one
+     * chunk per lane (as many lanes as the row has chunks, up to 32); 0 =
+     * auto (4 lanes for rows of up to 1 KB, else 8). The FP32 partial sums
+     * are added in an order that depends on it, so keys of non-integer data
+     * can differ in the last bits between settings; integer-valued data
+     * gives identical keys. */
+    int32_t team_lanes;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

@@ -242,6 +242,28 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
     // auto: the direct-mapped cache for the one-CTA sync kernel (measured 1-5 % faster), else open addressing
     a.visited_mode = p->visited_mode == 0 ? ((async || csize > 1) ? 0 : 1) : p->visited_mode - 1;
+    if (p->l2_prefetch < 0 || p->l2_prefetch > 2)
+        return fail(ANN_ERR_ARG, "l2_prefetch=%d not in {0, 1, 2}", p->l2_prefetch);
+    a.l2_prefetch = p->l2_prefetch != 2;
+    {
+        const int tl = p->team_lanes;
+        if (!(tl == -1 || tl == 0 || (tl > 0 && tl <= 32 && (tl & (tl - 1)) == 0)))
+            return fail(ANN_ERR_ARG, "team_lanes=%d must be -1, 0 or a power of two up to 32", tl);
+        auto log2_team = [tl](int cpr) {  // cpr = 16-byte chunks per row
+            int ts = tl;
+            if (tl == -1) {  // one chunk per lane
+                ts = 1;
+                while (ts < cpr && ts < 32) ts <<= 1;
+            } else if (tl == 0) {  // auto: 4 lanes for rows of up to 64 chunks (1 KB), else 8 (measured best)
+                ts = cpr <= 64 ? 4 : 8;
+            }
+            int lts = 0;
+            while ((1 << lts) < ts) ++lts;
+            return lts;
+        };
+        a.team_lanes = log2_team(x.d_pad * ann::storage_bytes(x.storage) / 16);
+        a.team_lanes32 = log2_team(x.d_pad32 * 4 / 16);
+    }
     if (p->stage_bytes < -1) return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
     if (p->lane_pipeline && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
         // per lane: 4 groups of 2 rows of its team in flight (compute_keys_pipe<.., U = 2, D = 4>)

@@ -58,6 +58,9 @@ struct SearchArgs {
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
     int32_t tma_rows;      // rows per bulk-copy staging batch (0 = gather rows through registers)
     int32_t pipe_bytes;    // per-CTA ring of the per-lane cp.async pipeline (0 = off)
+    int32_t l2_prefetch;   // 1 = bulk L2 prefetch of each candidate row once it passes the visited filter
+    int32_t team_lanes;    // distance gather: log2 of the lanes that share one candidate row
+    int32_t team_lanes32;  // the same for the FP32 rows of the re-rank
     int64_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t row_bytes = (uint32_t)a.d_pad * (STORE == ANN_STORE_F32 ? 4u : STORE == ANN_STORE_E4M3 ? 1u : 2u);
     int off[10];
     cluster_smem_bytes(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, off);
     float *qv = reinterpret_cast<float *>(smem + off[0]);
@@ -179,13 +180,18 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
             int basepos = 0;
             if (lane == 0 && bal) basepos = atomicAdd(&ctl.ncand, __popc(bal));
             basepos = __shfl_sync(kFull, basepos, 0);
-            if (fresh) cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+            if (fresh) {
+                cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+                if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u);
+            }
         }
         __syncthreads();
         const int nc = ctl.ncand;
         if (tid == 0) ctl.hash_count += nc;
         const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
-        if (nc > 0) compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, pub[par], &ctl.nloc);
+        if (nc > 0)
+            compute_keys_teams<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, a.team_lanes, limit,
+                                          pub[par], &ctl.nloc);
         __syncthreads();
         if (tid == 0) {
             ctl.pub_n[par] = ctl.nloc;
@@ -237,7 +243,11 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
         const int qlen = ctl.qlen;
         const entry_t *res = Q;
         if (a.rerank) {
-            for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
+            for (int i = tid; i < qlen; i += NT) {
+                const uint32_t id = entry_id(Q[i]);
+                cand[i] = (entry_t)id;
+                if (a.l2_prefetch) prefetch_row_l2(a.base32, (uint32_t)a.d_pad32 * 4u, id);
+            }
             __syncthreads();
             compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
             int P = 32;

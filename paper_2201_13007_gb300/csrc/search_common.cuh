@@ -119,6 +119,15 @@ template <> struct Chunk<ANN_STORE_E4M3> {
     }
 };
 
+// Ask for one row (bytes a multiple of 16, 16-byte aligned start) to be
+// brought into L2 by the bulk-copy unit; no completion is tracked and no
+// register is held, so every row of a step can be in flight at once.
+__device__ __forceinline__ void prefetch_row_l2(const void *rows, uint32_t row_bytes, uint32_t id) {
+    const char *p = static_cast<const char *>(rows) + (size_t)id * row_bytes;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(row_bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ uint4 ld_row_chunk(const uint4 *p) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -191,6 +200,54 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
                 if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
             }
         }
+    }
+}
+
+// Same contract as the filtered compute_keys, with teams of ts lanes (a
+// power of two, 1..32) per row and each lane walking its own chunks of the
+// row (chunk tl, tl + ts, ...), G of them in flight per round. A warp covers
+// 32 / ts rows at once, so the shuffle reduction (log2 ts levels) and the
+// append are paid once per 32 / ts rows; with small teams that is far fewer
+// instructions per row than one chunk per lane.
+template <int STORE, int NT, int G = 2>
+__device__ __forceinline__ void compute_keys_teams(const void *rows, const float *scales, int row_elems, int metric,
+                                                   const float *qv, const entry_t *cand, int nc, int lts,
+                                                   entry_t limit, entry_t *out, int *out_n) {
+    constexpr int NW = NT / 32;
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ts = 1 << lts, rpw = 32 >> lts;
+    const int cpr = row_elems / EPC;
+    const int team = lane >> lts, tl = lane & (ts - 1);
+    const bool l2 = metric == ANN_METRIC_L2;
+    const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
+    for (int c0 = warp * rpw; c0 < nc; c0 += NW * rpw) {
+        const int c = c0 + team;
+        const bool valid = c < nc;
+        const uint32_t id = valid ? (uint32_t)(cand[c] & 0xFFFFFFFFull) : 0u;
+        const float sc = (STORE == ANN_STORE_E4M3 && valid) ? __ldg(scales + id) : 1.f;
+        const uint4 *rp = rbase + (size_t)id * cpr;
+        float2 acc = make_float2(0.f, 0.f);
+        if (valid) {
+            for (int ch0 = tl; ch0 < cpr; ch0 += ts * G) {
+                uint4 v[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) v[g] = ld_row_chunk(rp + ch0 + g * ts);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) Chunk<STORE>::add(acc, v[g], qv + (ch0 + g * ts) * EPC, sc, l2);
+            }
+        }
+        float r = acc.x + acc.y;
+        for (int off = ts >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+        const entry_t e = pack_entry(l2 ? r : -r, id);
+        const bool keep = tl == 0 && valid && e < limit;
+        const unsigned bal = __ballot_sync(kFull, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
     }
 }
 

@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 int basepos = 0;
                 if (lane == 0 && bal) basepos = atomicAdd(&ctl.ncand, __popc(bal));
                 basepos = __shfl_sync(kFull, basepos, 0);
-                if (fresh) cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+                if (fresh) {
+                    cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+                    if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u);
+                }
             }
             __syncthreads();
             ANN_PHASE(1)
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                                                  &ctl.ns);
                     __syncthreads();
                 } else {
-                    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, limit, surv, &ctl.ns);
+                    compute_keys_teams<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, a.team_lanes,
+                                                  limit, surv, &ctl.ns);
                     __syncthreads();
                 }
                 ANN_PHASE(2)
@@ -305,15 +309,22 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         // --- output: first k of the queue, optionally re-ranked with FP32 rows
         const entry_t *res = Q;
         if (a.rerank) {
-            for (int i = tid; i < qlen; i += NT) cand[i] = (entry_t)entry_id(Q[i]);
+            for (int i = tid; i < qlen; i += NT) {
+                const uint32_t id = entry_id(Q[i]);
+                cand[i] = (entry_t)id;
+                if (a.l2_prefetch) prefetch_row_l2(a.base32, (uint32_t)a.d_pad32 * 4u, id);
+            }
+            if (tid == 0) ctl.ns = 0;
             __syncthreads();
-            compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
+            // every key is kept (limit = the empty entry), in whatever order the teams finish
+            compute_keys_teams<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen, a.team_lanes32,
+                                                  kEmptyEntry, surv, &ctl.ns);
             int P = 32;
             while (P < qlen) P <<= 1;
-            for (int i = qlen + tid; i < P; i += NT) cand[i] = kEmptyEntry;
+            for (int i = qlen + tid; i < P; i += NT) surv[i] = kEmptyEntry;
             __syncthreads();
-            block_bitonic_sort<NT>(cand, P);
-            res = cand;
+            block_bitonic_sort<NT>(surv, P);
+            res = surv;
         }
         int64_t *oid = a.out_ids + (size_t)qi * a.k;
         float *odist = a.out_dists + (size_t)qi * a.k;

@@ -280,3 +280,68 @@ def test_lane_pipeline_exact(ann, oracle_mod, sift_small, storage, threads):
                                                 M0=1, M_max=M, t=1, nthreads=8)
         compare_exact(ids, dists, o_ids, o_keys)
         np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
+
+
+_TEAM_ORACLE = {}
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("team_lanes", [-1, 1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("l2_prefetch", [1, 2])
+def test_team_sizes_exact(ann, oracle_mod, sift_small, storage, team_lanes, l2_prefetch):
+    """Any number of lanes per row in the distance gather (with or without
+    the L2 prefetch of fresh rows) gives exactly the oracle's ids, keys and
+    distance counts on integer data; the re-rank's FP32 rows take the same
+    team size rule."""
+    _, Index, stats_dict = ann
+    w = sift_small
+    for L, M in ((64, 4), (200, 16), (128, 32)):
+        ids, dists, st = _run(Index, w, storage=storage, keep_f32=storage != "f32", L=L, M=M, hash_bits=15,
+                              visited_mode=1, team_lanes=team_lanes, l2_prefetch=l2_prefetch,
+                              rerank=storage != "f32")
+        if (L, M) not in _TEAM_ORACLE:
+            _TEAM_ORACLE[(L, M)] = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
+                                                     M0=1, M_max=M, t=1, nthreads=8)
+        o_ids, o_keys, o_st = _TEAM_ORACLE[(L, M)]
+        compare_exact(ids, dists, o_ids, o_keys)
+        np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "e4m3"])
+@pytest.mark.parametrize("team_lanes", [1, 4, 32])
+def test_team_sizes_float_ragged_rows(ann, oracle_mod, storage, team_lanes):
+    """Float data with d = 200: rows whose chunk count is not a multiple of
+    the team size times the chunks in flight (ragged last round per lane).
+    Keys follow the oracle on the stored values within the FP32 error bound;
+    the FP32 re-rank of the final queue equals the oracle's re-rank."""
+    _, Index, _ = ann
+    w = synth.make_workload("gist", 6000, 48, d=200)
+    L, M = 64, 8
+    stored = oracle_mod.stored_values(w.base, storage)
+    ix = Index(w.base, w.adj, w.entry, storage=storage, keep_f32=storage != "f32")
+    q = torch.from_numpy(w.queries).cuda()
+    ids, d = ix.search(q, L, L, M, hash_bits=15, team_lanes=team_lanes)
+    torch.cuda.synchronize()
+    o_ids, o_keys, o_st = oracle_mod.search(stored, w.adj, w.entry, w.queries, algo="topm", L=L, K=L,
+                                            M0=1, M_max=M, t=1, nthreads=8,
+                                            tie_tol=fp32_tie_window(stored, w.queries, "l2")[0])
+    compare_float(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_keys, o_st["tie_events"], stored, w.queries, "l2")
+    if storage != "f32":
+        ids_rr, d_rr = ix.search(q, 10, L, M, hash_bits=15, rerank=True, team_lanes=team_lanes)
+        torch.cuda.synchronize()
+        clean = o_st["tie_events"] == 0
+        r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, o_ids, 10)
+        compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
+                      np.zeros(clean.sum()), w.base, w.queries[clean], "l2")
+    ix.close()
+
+
+def test_gather_option_errors(ann, tiny):
+    pkg, Index, _ = ann
+    ix = Index(tiny.base, tiny.adj, tiny.entry)
+    q = torch.from_numpy(tiny.queries).cuda()
+    for bad in (dict(team_lanes=3), dict(team_lanes=64), dict(team_lanes=-2), dict(l2_prefetch=3),
+                dict(l2_prefetch=-1)):
+        with pytest.raises(pkg.AnnError):
+            ix.search(q, 10, 64, 4, **bad)
+    ix.close()
