@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default="sift", choices=["sift", "gist", "deep-batch", "serve"],
                     help="sift: the headline (default); the others measure the precision, batching and serving "
                          "workloads and print one JSON line each")
+    ap.add_argument("--kernel-digest", action="store_true",
+                    help="print the digest of the CUDA sources that an ncu summary records, and exit")
     return ap.parse_args()
 
 
@@ -166,19 +168,33 @@ def max_over_ranks(torch, dist, seconds, device="cuda"):
     return float(t.item())
 
 
+def kernel_sources_digest():
+    """Short SHA-256 of the CUDA sources and the C header: an ncu figure is
+    only reused while the code it was taken from is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_13007_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in files + [os.path.join(ROOT, "include", "ann.h")]:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel_label):
     """DRAM bytes per launch (read + write) from the committed ncu summary of
     the headline kernel, if that summary was taken with this exact launch
-    configuration; else None."""
+    configuration and these exact kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "sync_search_kernel_sift1m_L640_M32_bf16.md")
     if not os.path.exists(p):
         return None
     vals = {}
     for line in open(p):
-        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "traffic_config"):
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "traffic_config", "traffic_sources"):
             k, v = line.split(":", 1)
             vals[k] = v.strip()
-    if vals.get("traffic_config") != kernel_label or "traffic_bytes_per_launch" not in vals:
+    if (vals.get("traffic_config") != kernel_label or vals.get("traffic_sources") != kernel_sources_digest()
+            or "traffic_bytes_per_launch" not in vals):
         return None
     return float(vals["traffic_bytes_per_launch"])
 
@@ -744,7 +760,9 @@ def run_serve(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernel_digest:
+        print(kernel_sources_digest())
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "gist":
         run_gist(args)

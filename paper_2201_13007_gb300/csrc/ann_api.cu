@@ -190,6 +190,13 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         return fail(ANN_ERR_ARG, "cluster=%d not in {0, 1, 2, 4, 8}", p->cluster);
     if (csize > 1 && async) return fail(ANN_ERR_ARG, "clusters are for sync mode only");
     int threads = p->threads;
+    // Automatic launch shape, from (threads, visited bits) sweeps on the 1M x 128 (10,000 queries)
+    // and 1M x 960 (1,000 queries) workloads. With at least 32 queries per SM the one-CTA sync
+    // kernel is fastest with small CTAs (more queries in flight per SM) and a 2^12-slot visited
+    // cache at every (L, M). With fewer queries each query's own latency counts: long queues or
+    // heavy steps (M * R rows of at least 256 KB) take 512 threads and 2^14 slots.
+    const bool many = !async && csize == 1 && nq >= 32LL * sm_count();
+    const bool heavy = L >= 384 || (int64_t)M * x.R * x.d_pad * ann::storage_bytes(x.storage) >= (256 << 10);
     if (async) {
         // one warp per walker: T = M walkers, at least two warps
         int walkers = 2;
@@ -199,15 +206,13 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
             return fail(ANN_ERR_ARG, "threads=%d not in {64,...,1024}", threads);
         if (threads / 32 < M) return fail(ANN_ERR_ARG, "async mode needs threads >= 32*M");
     } else {
-        // measured on the 1M x 128 workload: long queues want more warps per
-        // query (more rows in flight per step), short ones more queries per SM
-        if (threads == 0) threads = L >= 384 ? 512 : (M * x.R >= 1024 ? 256 : 128);
+        if (threads == 0) threads = many ? (M * x.R >= 1024 ? 256 : 128) : (heavy ? 512 : (M * x.R >= 1024 ? 256 : 128));
         if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
             return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
         if (csize > 1 && threads == 64) threads = 128;
     }
     int hb = p->hash_bits;
-    if (hb == 0) hb = L >= 384 ? 14 : (M * x.R >= 1024 ? 13 : 12);
+    if (hb == 0) hb = many ? 12 : (heavy ? 14 : (M * x.R >= 1024 ? 13 : 12));
     if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
 
     ann::SearchArgs &a = plan->a;

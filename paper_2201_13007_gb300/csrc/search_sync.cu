@@ -105,13 +105,17 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         const float *qg = a.queries + (size_t)qi * a.d;
         for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
         for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
-        if (tid == 0) cand[0] = (entry_t)(uint32_t)a.entry;
+        if (tid == 0) {
+            cand[0] = (entry_t)(uint32_t)a.entry;
+            ctl.ns = 0;
+        }
         __syncthreads();
         // the entry point P: distance, queue = [P], visited = {P}
-        compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, 1);
+        compute_keys_teams<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, 1, a.team_lanes, kEmptyEntry,
+                                      surv, &ctl.ns);
         __syncthreads();
         if (tid == 0) {
-            Qa[0] = cand[0];
+            Qa[0] = surv[0];
             visited_insert(table, a.hash_bits, (uint32_t)a.entry);
             ctl.hash_count = 1;
         }
@@ -175,14 +179,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             }
 
             // --- expand: adjacency rows -> visited filter -> candidate ids
-            const int total = nact * R;
-            for (int b = warp * 32; b < total; b += NT) {
-                const int i = b + lane;
-                int u = -1;
-                if (i < total) {
-                    const int aidx = i / R, r = i - aidx * R;
-                    u = __ldg(a.adj + (size_t)act[aidx] * R + r);
-                }
+            // (warp-uniform call: visited test, warp-aggregated append, L2 prefetch of the fresh row)
+            auto visit = [&](int u) {
                 int ins = 0;
                 if (u >= 0)
                     ins = a.visited_mode == 0 ? visited_insert(table, a.hash_bits, (uint32_t)u)
@@ -196,6 +194,26 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 if (fresh) {
                     cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
                     if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u);
+                }
+            };
+            {
+                // each thread issues all of its adjacency loads (up to four) before any visited update
+                constexpr int KA = 4;
+                const int total = nact * R;
+                for (int b0 = warp * 32; b0 < total; b0 += NT * KA) {
+                    int u[KA];
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) {
+                        const int i = b0 + k * NT + lane;
+                        u[k] = -1;
+                        if (i < total) {
+                            const int aidx = i / R, r = i - aidx * R;
+                            u[k] = __ldg(a.adj + (size_t)act[aidx] * R + r);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < KA; ++k)
+                        if (b0 + k * NT < total) visit(u[k]);  // warp-uniform
                 }
             }
             __syncthreads();
