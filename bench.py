@@ -318,6 +318,12 @@ def run_ours(args):
             svc = (st[:, 7] - st[:, 6]) / 1e3
             row_bytes = ix.info()["d_pad"] * es
             b = algorithmic_bytes(st, w.R, row_bytes, w.d, K, L if kw.get("rerank") else 0)
+            # the same point with an exact visited set (open addressing, 2^15 slots, no reset at these
+            # sizes): the fewest distance evaluations the method needs, untimed
+            sx = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
+            ix.search(q, K, L, M, stats=sx, **dict(kw, visited_mode=1, hash_bits=15))
+            sx = sx.cpu().numpy()
+            bx = algorithmic_bytes(sx, w.R, row_bytes, w.d, K, L if kw.get("rerank") else 0)
             results[(name, tgt)] = {
                 "launch": ix.describe(nq, K, L, M, **kw),
                 "L": L, "M": M, "recall": recall_at_k(ids, gt), "ms_per_step": t * 1e3,
@@ -325,6 +331,9 @@ def run_ours(args):
                 "p99_us": float(np.percentile(svc, 99)), "alg_bytes": b, "gbs": b / t / 1e9,
                 "evals_per_query": float(st[:, 2].mean()), "steps_per_query": float(st[:, 0].mean()),
                 "hash_resets_per_query": float(st[:, 3].mean()),
+                "alg_bytes_exact_visited": bx, "gbs_exact_visited": bx / t / 1e9,
+                "evals_per_query_exact_visited": float(sx[:, 2].mean()),
+                "exact_visited_resets": float(sx[:, 3].sum()),
             }
     clocks = clk.summary()
 
@@ -412,7 +421,11 @@ def run_ours(args):
                      "traffic_source": "profiles/sync_search_kernel_sift1m_L640_M32_bf16.md (one ncu capture, "
                                        "dram__bytes_read.sum + dram__bytes_write.sum per launch)",
                      "kernel": klabel,
-                     "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 (re-rank) + d*4 + k*12"},
+                     "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 (re-rank) + d*4 + k*12",
+                     "evals_per_query": h["evals_per_query"],
+                     "achieved_exact_visited": h["gbs_exact_visited"],
+                     "frac_exact_visited": h["gbs_exact_visited"] / hbm,
+                     "evals_per_query_exact_visited": h["evals_per_query_exact_visited"]},
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * w.d * 4,
                 "d2h_bytes_per_step": nq * K * 12},
         "gpu_launches": args.steps,
