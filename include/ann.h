@@ -154,7 +154,7 @@ typedef struct {
     int32_t l2_prefetch;
     /* Sync kernels (one CTA or one cluster per query), distance gather:
      * lanes that share one candidate row, a power of two from 1 to 32. Each
-     * lane streams its own 16-byte chunks of the row (two in flight) and the
+     * lane streams its own 16-byte chunks of the row (four in flight) and the
      * team adds its partial sums with log2(team_lanes) shuffles. -1 = one
      * chunk per lane (as many lanes as the row has chunks, up to 32); 0 =
      * auto (4 lanes for rows of up to 1 KB, else 8). The FP32 partial sums
