@@ -402,7 +402,8 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     h = results[head]
     klabel = (f"sync_search_kernel<{h['launch']['threads']}, {'BF16' if head[0].startswith('batched') else 'F32'}>, "
-              f"grid {h['launch']['grid']}, {h['launch']['smem_bytes']} B shared, 2^{h['launch']['hash_bits']} visited slots")
+              f"grid {h['launch']['grid']}, {h['launch']['smem_bytes']} B shared, 2^{h['launch']['hash_bits']} visited slots "
+              f"of {h['launch']['visited_slot_bytes']} B")
     out = {
         "metric": "QPS at recall@10>=0.99 (batched BF16 + FP32 re-rank, 1M x 128)",
         "value": h["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,

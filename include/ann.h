@@ -126,11 +126,16 @@ typedef struct {
      * These are the Expand / Merge / Seq parts of the paper's time
      * breakdown (Fig. 14). */
     int64_t *phase_cycles;
-    /* Visited set: 1 = open-addressing table, exact until it is half full,
-     * then reset to the queued ids; 2 = direct-mapped cache that forgets a
-     * vertex when another one hashes to its slot (one-CTA sync kernel only);
-     * 0 = auto (2 for the one-CTA sync kernel, else 1). Both only ever
-     * forget, which changes the number of distance evaluations but never the
+    /* Visited set: 1 = open-addressing table of ids, exact until it is half
+     * full, then reset to the queued ids; 2 = direct-mapped cache that
+     * forgets a vertex when another one hashes to its slot, storing in each
+     * slot only the bits of the (bijectively) hashed id that the slot index
+     * does not already fix: one byte per slot while the ids need at most
+     * hash_bits + 7 bits, two bytes up to hash_bits + 15, else a full id;
+     * 3 = the same cache with a full 32-bit id per slot. 2 and 3 are for the
+     * one-CTA sync kernel only. 0 = auto (2 for the one-CTA sync kernel, else
+     * 1). No form ever reports a vertex it did not see; they only forget,
+     * which changes the number of distance evaluations but never the
      * results. */
     int32_t visited_mode;
     /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: shared memory for
@@ -214,6 +219,7 @@ typedef struct {
     int32_t hash_bits;    /* log2 slots of the visited table */
     int32_t cluster;      /* CTAs per query */
     int32_t mode;         /* ann_mode */
+    int32_t visited_slot_bytes; /* bytes per visited-set slot: 1 or 2 (tags), 4 (ids) */
 } ann_launch_info;
 
 int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L, int32_t M,

@@ -74,7 +74,8 @@ class Result(ctypes.Structure):
 
 class LaunchInfo(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("hash_bits", ctypes.c_int32), ("cluster", ctypes.c_int32), ("mode", ctypes.c_int32)]
+                ("hash_bits", ctypes.c_int32), ("cluster", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("visited_slot_bytes", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

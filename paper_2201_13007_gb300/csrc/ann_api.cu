@@ -211,8 +211,32 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
             return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
         if (csize > 1 && threads == 64) threads = 128;
     }
+    // visited set: 1 = open addressing; 2 = direct-mapped cache of tags; 3 = direct-mapped cache of ids
+    if (p->visited_mode < 0 || p->visited_mode > 3)
+        return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2, 3}", p->visited_mode);
+    if (p->visited_mode >= 2 && (async || csize > 1))
+        return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
+    const int vmode = p->visited_mode == 0 ? ((async || csize > 1) ? 1 : 2) : p->visited_mode;
+    int idbits = 1;  // bits of the largest vertex id
+    while (idbits < 31 && (int64_t(1) << idbits) < x.n) ++idbits;
+    auto slot_bytes_for = [&](int bits) {
+        if (vmode != 2) return 4;
+        const int tb = idbits > bits ? idbits - bits : 0;
+        return tb <= 7 ? 1 : (tb <= 15 ? 2 : 4);
+    };
     int hb = p->hash_bits;
-    if (hb == 0) hb = many ? 12 : (heavy ? 14 : (M * x.R >= 1024 ? 13 : 12));
+    if (hb == 0) {
+        if (many) {  // the most slots that fit in 16 KB (2^12 full ids; 2^14 one-byte tags)
+            hb = 12;
+            for (int b = 14; b > 12; --b)
+                if ((1 << b) * slot_bytes_for(b) <= (16 << 10)) {
+                    hb = b;
+                    break;
+                }
+        } else {
+            hb = heavy ? 14 : (M * x.R >= 1024 ? 13 : 12);
+        }
+    }
     if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
 
     ann::SearchArgs &a = plan->a;
@@ -241,12 +265,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.R_ratio = p->R_ratio;
     a.rerank = p->rerank ? 1 : 0;
     a.hash_bits = hb;
-    if (p->visited_mode < 0 || p->visited_mode > 2)
-        return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2}", p->visited_mode);
-    if (p->visited_mode == 2 && (async || csize > 1))
-        return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
-    // auto: the direct-mapped cache for the one-CTA sync kernel (measured 1-5 % faster), else open addressing
-    a.visited_mode = p->visited_mode == 0 ? ((async || csize > 1) ? 0 : 1) : p->visited_mode - 1;
+    // auto: the direct-mapped tag cache for the one-CTA sync kernel, else open addressing
+    a.visited_mode = vmode >= 2 ? 1 : 0;
     if (p->l2_prefetch < 0 || p->l2_prefetch > 2)
         return fail(ANN_ERR_ARG, "l2_prefetch=%d not in {0, 1, 2}", p->l2_prefetch);
     a.l2_prefetch = p->l2_prefetch != 2;
@@ -298,11 +318,14 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         if (csize > 1) return ann::cluster_smem_size(a.qfloats, a.Lcap, a.Ccap, bits, M);
         return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
                      : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M,
-                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage) + a.pipe_bytes).total;
+                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage) + a.pipe_bytes,
+                                        slot_bytes_for(bits)).total;
     };
     int smem = smem_for(a.hash_bits);
     // an automatic visited table shrinks until the layout fits (it may then forget more often)
     while (p->hash_bits == 0 && smem > max_dyn_smem() && a.hash_bits > 10) smem = smem_for(--a.hash_bits);
+    a.slot_bytes = slot_bytes_for(a.hash_bits);
+    a.tag_bits = a.slot_bytes < 4 && idbits > a.hash_bits ? idbits - a.hash_bits : 0;
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
                     smem, max_dyn_smem());
@@ -451,6 +474,7 @@ int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L
     out->hash_bits = plan.a.hash_bits;
     out->cluster = plan.cluster;
     out->mode = plan.mode;
+    out->visited_slot_bytes = plan.a.slot_bytes;
     return ANN_OK;
 }
 

@@ -56,6 +56,8 @@ struct SearchArgs {
     int32_t rerank;
     int32_t hash_bits;
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
+    int32_t slot_bytes;    // direct-mapped slot: 4 = a full id; 1 or 2 = a tag (the hashed id's bits below the index)
+    int32_t tag_bits;      // bits of the tag when slot_bytes < 4
     int32_t tma_rows;      // rows per bulk-copy staging batch (0 = gather rows through registers)
     int32_t pipe_bytes;    // per-CTA ring of the per-lane cp.async pipeline (0 = off)
     int32_t l2_prefetch;   // 1 = bulk L2 prefetch of each candidate row once it passes the visited filter
@@ -82,7 +84,7 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
-                                                  int stage_bytes = 0) {
+                                                  int stage_bytes = 0, int slot_bytes = 4) {
     SmemLayout s;
     int o = 0;
     s.q_off = o;    o += align16(qfloats * 4);
@@ -91,7 +93,7 @@ __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Cca
     s.cand_off = o; o += align16(Ccap * 8);
     s.cand2_off = o; o += align16(Ccap * 8);
     s.dup_off = o;  o += align16(Ccap);
-    s.hash_off = o; o += align16((1 << hash_bits) * 4);
+    s.hash_off = o; o += align16((1 << hash_bits) * slot_bytes);
     s.act_off = o;  o += align16(Mcap * 4);
     s.bar_off = o;  o += 16;
     s.stage_off = o; o += align16(stage_bytes);

@@ -281,6 +281,38 @@ __device__ __forceinline__ int visited_exchange(uint32_t *table, int bits, uint3
     return old == kEmptySlot ? 1 : 3;
 }
 
+// Direct-mapped cache of W-byte tags (W = 1 or 2) over 2^bits slots. With
+// b = bits + tag_bits >= the bits of any id, h = (id * odd constant) mod 2^b
+// is a bijection on [0, 2^b): the top `bits` of h choose the slot and the low
+// tag_bits of h are stored there (plus one; 0 = empty). (slot, tag) therefore
+// names exactly one id: a slot never claims a vertex it did not see, it can
+// only forget one when another takes its slot. Slots are updated with a
+// 32-bit CAS on the word that holds them. Returns 0 if the id was present,
+// 1 if it went into an empty slot, 3 if it replaced another vertex (or the
+// CAS kept losing, which is treated the same way: a forgotten vertex only
+// costs a repeated distance, and the merge drops an id that is queued twice).
+template <int W>
+__device__ __forceinline__ int visited_tag(uint32_t *table, int bits, int tag_bits, uint32_t id) {
+    constexpr int PER = 4 / W;
+    constexpr uint32_t MASK = W == 1 ? 0xFFu : 0xFFFFu;
+    const int b = bits + tag_bits;
+    uint32_t h = id * 0x9E3779B1u;
+    if (b < 32) h &= (1u << b) - 1u;
+    const uint32_t slot = h >> tag_bits;
+    const uint32_t tag = (h & ((1u << tag_bits) - 1u)) + 1u;
+    uint32_t *wp = table + slot / PER;
+    const int sh = (int)(slot % PER) * 8 * W;
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(wp);
+    for (int it = 0; it < 32; ++it) {
+        const uint32_t cur = (old >> sh) & MASK;
+        if (cur == tag) return 0;
+        const uint32_t prev = atomicCAS(wp, old, (old & ~(MASK << sh)) | (tag << sh));
+        if (prev == old) return cur == 0u ? 1 : 3;
+        old = prev;
+    }
+    return 3;
+}
+
 // ------------------------------------------------------------ bitonic sort
 __device__ __forceinline__ entry_t cmpx(entry_t v, int j, int k, int i) {
     entry_t p = __shfl_xor_sync(kFull, v, j);

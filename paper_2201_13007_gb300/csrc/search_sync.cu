@@ -42,6 +42,16 @@ struct Ctrl {
     long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
 };
 
+// One insert into the query's visited set, whichever form it has: 0 = was
+// present, 1 = inserted, 2 or 3 = inserted while another vertex may have been
+// forgotten (probe limit, eviction).
+__device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, uint32_t id) {
+    if (a.visited_mode == 0) return visited_insert(table, a.hash_bits, id);
+    if (a.slot_bytes == 1) return visited_tag<1>(table, a.hash_bits, a.tag_bits, id);
+    if (a.slot_bytes == 2) return visited_tag<2>(table, a.hash_bits, a.tag_bits, id);
+    return visited_exchange(table, a.hash_bits, id);
+}
+
 template <int NT, int STORE>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(const SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -49,7 +59,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row_bytes = a.d_pad * (STORE == ANN_STORE_F32 ? 4 : STORE == ANN_STORE_E4M3 ? 1 : 2);
     const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M,
-                                       a.tma_rows * row_bytes + a.pipe_bytes);
+                                       a.tma_rows * row_bytes + a.pipe_bytes, a.slot_bytes);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + lay.bar_off);
     unsigned char *stage = smem + lay.stage_off;
     unsigned parity = 0;
@@ -104,7 +114,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         // query into shared memory, zero padded; clear the visited table
         const float *qg = a.queries + (size_t)qi * a.d;
         for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
-        for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
+        {
+            const int words = (H * a.slot_bytes) >> 2;
+            const uint32_t empty = a.slot_bytes < 4 ? 0u : kEmptySlot;
+            for (int i = tid; i < words; i += NT) table[i] = empty;
+        }
         if (tid == 0) {
             cand[0] = (entry_t)(uint32_t)a.entry;
             ctl.ns = 0;
@@ -116,7 +130,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         __syncthreads();
         if (tid == 0) {
             Qa[0] = surv[0];
-            visited_insert(table, a.hash_bits, (uint32_t)a.entry);
+            visit_set(table, a, (uint32_t)a.entry);
             ctl.hash_count = 1;
         }
         __syncthreads();
@@ -201,8 +215,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
 #pragma unroll
                     for (int k = 0; k < KA; ++k) {
                         if (u[k] >= 0) {
-                            const int ins = a.visited_mode == 0 ? visited_insert(table, a.hash_bits, (uint32_t)u[k])
-                                                                : visited_exchange(table, a.hash_bits, (uint32_t)u[k]);
+                            const int ins = visit_set(table, a, (uint32_t)u[k]);
                             if (ins != 0) fresh |= 1u << k;
                             if (ins >= 2) forgot = true;
                         }

@@ -235,13 +235,19 @@ def test_reduced_precision_with_rerank(ann, oracle_mod, storage):
     ix.close()
 
 
+@pytest.mark.parametrize("visited_mode,slot_bytes", [(2, 1), (3, 4)])
 @pytest.mark.parametrize("hash_bits", [8, 10, 12])
-def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash_bits):
+def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash_bits, visited_mode, slot_bytes):
     """The direct-mapped visited cache forgets a vertex whenever another one
-    hashes to its slot; ids and keys must still be exact (reading 14)."""
+    hashes to its slot; ids and keys must still be exact (reading 14). Mode 2
+    keeps a one-byte tag per slot here (20,000 ids need 15 bits), mode 3 a
+    full id."""
     _, Index, stats_dict = ann
     w = sift_small
-    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=2)
+    ix = Index(w.base, w.adj, w.entry)
+    assert ix.describe(64, 10, 128, 8, hash_bits=hash_bits, visited_mode=visited_mode)["visited_slot_bytes"] == slot_bytes
+    ix.close()
+    ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=visited_mode)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
                                             M0=1, M_max=8, t=1, nthreads=8)
     compare_exact(ids, dists, o_ids, o_keys)
@@ -345,3 +351,20 @@ def test_gather_option_errors(ann, tiny):
         with pytest.raises(pkg.AnnError):
             ix.search(q, 10, 64, 4, **bad)
     ix.close()
+
+
+@pytest.mark.parametrize("hash_bits,slot_bytes", [(8, 2), (9, 2), (10, 1)])
+def test_two_byte_visited_tags_exact(ann, oracle_mod, hash_bits, slot_bytes):
+    """70,000 vertices need 17 id bits, so 2^8 / 2^9 / 2^10 slots leave tags
+    of 9 / 8 / 7 bits: two bytes per slot, two bytes, one byte. Results stay
+    exact on integer data."""
+    _, Index, stats_dict = ann
+    w = synth.make_workload("sift", 70000, 48)
+    ix = Index(w.base, w.adj, w.entry)
+    assert ix.describe(48, 10, 96, 8, hash_bits=hash_bits, visited_mode=2)["visited_slot_bytes"] == slot_bytes
+    ix.close()
+    ids, dists, st = _run(Index, w, L=96, M=8, hash_bits=hash_bits, visited_mode=2)
+    o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=96, K=10,
+                                            M0=1, M_max=8, t=1, nthreads=8)
+    compare_exact(ids, dists, o_ids, o_keys)
+    assert (stats_dict(st)["evals"] >= o_st["evals"]).all()
