@@ -444,6 +444,44 @@ __device__ __forceinline__ entry_t warp_sort32(entry_t v) {
     return v;
 }
 
+// Ascending sort of in[0..n), 32 < n <= NT, into out[0..n) (disjoint from
+// in). Warp w sorts the run in[32w, 32w + 32) in registers and writes it
+// back; each element's rank is then its lane plus, for every other run, the
+// entries of that run below it (runs after its own) or not above it (runs
+// before its own), by a branch-free binary search. Equal entries thus keep
+// run order and every rank is distinct. Two barriers instead of the
+// log^2-many of a bitonic sort. Ends with a __syncthreads().
+template <int NT>
+__device__ void block_rank_sort(entry_t *in, int n, entry_t *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = (n + 31) >> 5;
+    entry_t v = kEmptyEntry;
+    if (warp < S) {
+        const int i = warp * 32 + lane;
+        v = warp_sort32(i < n ? in[i] : kEmptyEntry);
+        in[i] = v;
+    }
+    __syncthreads();
+    if (warp < S && v != kEmptyEntry) {
+        int r = lane;
+        for (int s = 0; s < S; ++s) {
+            if (s == warp) continue;
+            const entry_t *A = in + 32 * s;
+            const bool before = s < warp;
+            int p = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const entry_t x = A[p + step - 1];
+                if (before ? x <= v : x < v) p += step;
+            }
+            if (p == 31 && (before ? A[31] <= v : A[31] < v)) p = 32;
+            r += p;
+        }
+        out[r] = v;
+    }
+    __syncthreads();
+}
+
 // Merge sorted, duplicate-free C[0..nc) into sorted Q[0..qlen) (all threads
 // of the block), keeping the first L entries in Qn. A candidate whose id is
 // already in Q is dropped; if it carries the checked flag the queued copy

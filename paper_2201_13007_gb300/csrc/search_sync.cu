@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 ANN_PHASE(2)
                 const int ns = ctl.ns;
                 if (ns > 0) {
-                    // --- sort the survivors by (key, id)
+                    // --- sort the survivors by (key, id) into srt
+                    entry_t *srt = surv;
                     if (ns <= 32) {
                         if (warp == 0) {
                             entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
@@ -288,6 +289,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                             surv[lane] = e;
                         }
                         __syncthreads();
+                    } else if (ns > 64 && ns <= NT) {
+                        // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
+                        block_rank_sort<NT>(surv, ns, cand);  // the candidate ids are not needed any more
+                        srt = cand;
                     } else {
                         int P = 64;
                         while (P < ns) P <<= 1;
@@ -300,8 +305,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                         // --- drop ids already queued or repeated (only after the table forgot)
                         int any = 0;
                         for (int j = tid; j < ns; j += NT) {
-                            const entry_t c = surv[j];
-                            bool d = (j > 0 && surv[j - 1] == c);
+                            const entry_t c = srt[j];
+                            bool d = (j > 0 && srt[j - 1] == c);
                             if (!d) {
                                 const int pos = count_below(Q, qlen, c);
                                 d = pos < qlen && (Q[pos] & kMask) == c;
@@ -315,9 +320,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                                 for (int b = 0; b < ns; b += 32) {
                                     const int j = b + lane;
                                     const bool keep = j < ns && !dup[j];
-                                    const entry_t c = j < ns ? surv[j] : 0ull;
+                                    const entry_t c = j < ns ? srt[j] : 0ull;
                                     const unsigned bal = __ballot_sync(kFull, keep);
-                                    if (keep) surv[outp + __popc(bal & ((1u << lane) - 1u))] = c;
+                                    if (keep) srt[outp + __popc(bal & ((1u << lane) - 1u))] = c;
                                     outp += __popc(bal);
                                 }
                                 if (lane == 0) ctl.anydup = outp;
@@ -330,11 +335,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     // --- merge queue and survivors by rank, truncate to L
                     for (int i = tid; i < qlen; i += NT) {
                         const entry_t e = Q[i];
-                        const int pos = i + count_below(surv, ncl, e & kMask);
+                        const int pos = i + count_below(srt, ncl, e & kMask);
                         if (pos < L) Qn[pos] = e;
                     }
                     for (int j = tid; j < ncl; j += NT) {
-                        const entry_t c = surv[j];
+                        const entry_t c = srt[j];
                         const int pos = j + count_below(Q, qlen, c);
                         if (pos < L) Qn[pos] = c;
                     }
