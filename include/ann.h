@@ -133,10 +133,10 @@ typedef struct {
      * does not already fix: one byte per slot while the ids need at most
      * hash_bits + 7 bits, two bytes up to hash_bits + 15, else a full id;
      * 3 = the same cache with a full 32-bit id per slot. 2 and 3 are for the
-     * one-CTA sync kernel only. 0 = auto (2 for the one-CTA sync kernel, else
-     * 1). No form ever reports a vertex it did not see; they only forget,
-     * which changes the number of distance evaluations but never the
-     * results. */
+     * one-CTA sync kernel only. 0 = auto (for the one-CTA sync kernel 2 when
+     * L >= 128, else 3; otherwise 1). No form ever reports a vertex it did
+     * not see; they only forget, which changes the number of distance
+     * evaluations but never the results. */
     int32_t visited_mode;
     /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: shared memory for
      * staging candidate rows with bulk copies (one cp.async.bulk per row,

@@ -216,7 +216,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2, 3}", p->visited_mode);
     if (p->visited_mode >= 2 && (async || csize > 1))
         return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
-    const int vmode = p->visited_mode == 0 ? ((async || csize > 1) ? 1 : 2) : p->visited_mode;
+    // auto: tags for queues of 128 or more (thousands of vertices visited: capacity pays), full ids below
+    // (a 2^12-id cache already holds what a short search visits, and its exchange is cheaper than a CAS)
+    const int vmode = p->visited_mode == 0 ? ((async || csize > 1) ? 1 : (L >= 128 ? 2 : 3)) : p->visited_mode;
     int idbits = 1;  // bits of the largest vertex id
     while (idbits < 31 && (int64_t(1) << idbits) < x.n) ++idbits;
     auto slot_bytes_for = [&](int bits) {
@@ -265,7 +267,6 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.R_ratio = p->R_ratio;
     a.rerank = p->rerank ? 1 : 0;
     a.hash_bits = hb;
-    // auto: the direct-mapped tag cache for the one-CTA sync kernel, else open addressing
     a.visited_mode = vmode >= 2 ? 1 : 0;
     if (p->l2_prefetch < 0 || p->l2_prefetch > 2)
         return fail(ANN_ERR_ARG, "l2_prefetch=%d not in {0, 1, 2}", p->l2_prefetch);
