@@ -482,6 +482,33 @@ __device__ void block_rank_sort(entry_t *in, int n, entry_t *out) {
     __syncthreads();
 }
 
+// Merge path: the first min(L, qlen + ns) entries of the merge of sorted
+// Q[0..qlen) (ordered with the checked flag masked off) and sorted S[0..ns)
+// (no entry of S equal to one of Q) go to out. Thread t owns a contiguous
+// range of output positions: one binary search on its starting diagonal
+// finds how many of its predecessors come from Q, then it merges its range
+// sequentially. No barrier inside.
+template <int NT>
+__device__ __forceinline__ void block_merge_path(const entry_t *Q, int qlen, const entry_t *S, int ns, entry_t *out,
+                                                 int L) {
+    const int total = min(L, qlen + ns);
+    const int per = (total + NT - 1) / NT;
+    const int d0 = threadIdx.x * per;
+    if (d0 >= total) return;
+    const int d1 = min(d0 + per, total);
+    int lo = max(0, d0 - ns), hi = min(d0, qlen);
+    while (lo < hi) {  // the smallest i with Q[i] after S[d0 - 1 - i]
+        const int i = (lo + hi) >> 1;
+        if ((Q[i] & kMask) < S[d0 - 1 - i]) lo = i + 1;
+        else hi = i;
+    }
+    int i = lo, j = d0 - lo;
+    for (int d = d0; d < d1; ++d) {
+        const bool takeQ = j >= ns || (i < qlen && (Q[i] & kMask) < S[j]);
+        out[d] = takeQ ? Q[i++] : S[j++];
+    }
+}
+
 // Merge sorted, duplicate-free C[0..nc) into sorted Q[0..qlen) (all threads
 // of the block), keeping the first L entries in Qn. A candidate whose id is
 // already in Q is dropped; if it carries the checked flag the queued copy

@@ -332,17 +332,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                             if (tid == 0) ctl.dropped += ns - ncl;
                         }
                     }
-                    // --- merge queue and survivors by rank, truncate to L
-                    for (int i = tid; i < qlen; i += NT) {
-                        const entry_t e = Q[i];
-                        const int pos = i + count_below(srt, ncl, e & kMask);
-                        if (pos < L) Qn[pos] = e;
-                    }
-                    for (int j = tid; j < ncl; j += NT) {
-                        const entry_t c = srt[j];
-                        const int pos = j + count_below(Q, qlen, c);
-                        if (pos < L) Qn[pos] = c;
-                    }
+                    // --- merge queue and survivors, truncated to L (merge path: one search per thread)
+                    block_merge_path<NT>(Q, qlen, srt, ncl, Qn, L);
                     __syncthreads();  // the new queue is complete; nothing of the old one is read again
                     qlen = min(L, qlen + ncl);
                     entry_t *tmp = Q;
