@@ -482,6 +482,46 @@ __device__ void block_rank_sort(entry_t *in, int n, entry_t *out) {
     __syncthreads();
 }
 
+// The k smallest of in[0..n) (k <= 32), ascending, at the front of the
+// returned array (fewer if n < k). Warp w sorts runs of 32 in registers and
+// keeps the first k of each in tmp; the c = ceil(n / 32) * k kept entries
+// contain the k smallest and are sorted by one warp (c <= 32), by
+// block_rank_sort into out (c <= NT), else by a bitonic sort over tmp. in is
+// read only before the first barrier, so out may be in. tmp holds at least
+// next_pow2(c) entries and out at least c. Ends with a __syncthreads().
+// Returns the array the result is in (out or tmp).
+template <int NT>
+__device__ entry_t *block_topk(const entry_t *in, int n, int k, entry_t *tmp, entry_t *out) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int runs = (n + 31) >> 5;
+    for (int r = warp; r < runs; r += NW) {
+        const int i = r * 32 + lane;
+        const entry_t v = warp_sort32(i < n ? in[i] : kEmptyEntry);
+        if (lane < k) tmp[r * k + lane] = v;
+    }
+    const int c = runs * k;
+    __syncthreads();
+    if (c <= 32) {
+        if (warp == 0) {
+            const entry_t v = warp_sort32(lane < c ? tmp[lane] : kEmptyEntry);
+            if (lane < k) out[lane] = v;
+        }
+        __syncthreads();
+        return out;
+    }
+    if (c <= NT) {
+        block_rank_sort<NT>(tmp, c, out);
+        return out;
+    }
+    int P = 64;
+    while (P < c) P <<= 1;
+    for (int i = c + threadIdx.x; i < P; i += NT) tmp[i] = kEmptyEntry;
+    __syncthreads();
+    block_bitonic_sort<NT>(tmp, P);
+    return tmp;
+}
+
 // Merge path: the first min(L, qlen + ns) entries of the merge of sorted
 // Q[0..qlen) (ordered with the checked flag masked off) and sorted S[0..ns)
 // (no entry of S equal to one of Q) go to out. Thread t owns a contiguous

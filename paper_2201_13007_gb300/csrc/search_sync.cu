@@ -357,14 +357,20 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             if (tid == 0) ctl.ns = 0;
             __syncthreads();
             // every key is kept (limit = the empty entry), in whatever order the teams finish
-            compute_keys_teams<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen, a.team_lanes32,
-                                                  kEmptyEntry, surv, &ctl.ns);
-            int P = 32;
-            while (P < qlen) P <<= 1;
-            for (int i = qlen + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+            compute_keys_teams<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen,
+                                                     a.team_lanes32, kEmptyEntry, surv, &ctl.ns);
             __syncthreads();
-            block_bitonic_sort<NT>(surv, P);
-            res = surv;
+            if (k <= 32) {
+                // only the k best are output: select them instead of sorting the whole queue
+                res = block_topk<NT>(surv, qlen, k, cand, surv);
+            } else {
+                int P = 32;
+                while (P < qlen) P <<= 1;
+                for (int i = qlen + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+                __syncthreads();
+                block_bitonic_sort<NT>(surv, P);
+                res = surv;
+            }
         }
         int64_t *oid = a.out_ids + (size_t)qi * a.k;
         float *odist = a.out_dists + (size_t)qi * a.k;
