@@ -32,6 +32,12 @@ def sift():
     return synth.make_workload("sift", 20000, 2000)
 
 
+@pytest.fixture(scope="module")
+def sift10k():
+    # 10,000 queries: the recall comparison of the nondeterministic walkers is made on at least 10 K queries
+    return synth.make_workload("sift", 20000, 10000)
+
+
 def _search(Index, w, L, M, R, k=10, storage="f32", **kw):
     ix = Index(w.base, w.adj, w.entry, storage=storage, metric=w.metric)
     q = torch.from_numpy(w.queries).cuda()
@@ -67,16 +73,20 @@ def _valid(ids, d, base, q):
 
 @pytest.mark.parametrize("L,M,R", [(32, 2, 0.8), (64, 4, 0.8), (128, 8, 0.9), (64, 8, float("inf")),
                                    (96, 16, 0.8), (64, 32, 0.9)])
-def test_multi_walker_recall_matches_oracle(Index, oracle_mod, sift, L, M, R):
-    ids, d, st = _search(Index, sift, L, M, R)
-    _valid(ids, d, sift.base, sift.queries)
-    gt, _ = oracle_mod.exact_knn(sift.base, sift.queries, 10, nthreads=8)
-    o_ids, _, o_st = oracle_mod.search(sift.base, sift.adj, sift.entry, sift.queries, algo="speedann", L=L,
+def test_multi_walker_recall_matches_oracle(Index, oracle_mod, sift10k, L, M, R):
+    w = sift10k
+    ids, d, st = _search(Index, w, L, M, R)
+    _valid(ids, d, w.base, w.queries)
+    if not hasattr(test_multi_walker_recall_matches_oracle, "gt"):
+        test_multi_walker_recall_matches_oracle.gt = oracle_mod.exact_knn(w.base, w.queries, 10, nthreads=8)[0]
+    gt = test_multi_walker_recall_matches_oracle.gt
+    o_ids, _, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="speedann", L=L,
                                        K=10, M0=1, M_max=M, R_ratio=R, nthreads=8)
     r_gpu = oracle_mod.recall(ids, gt).mean()
     r_orc = oracle_mod.recall(o_ids, gt).mean()
-    # 2,000 queries x k=10: one id is worth 5e-5 of recall
-    assert abs(r_gpu - r_orc) <= 0.005, (r_gpu, r_orc)
+    print(f"L={L} M={M} R={R}: recall GPU {r_gpu:.5f} oracle {r_orc:.5f} gap {r_gpu - r_orc:+.5f}")
+    # 10,000 queries x k = 10: one id is worth 1e-5 of recall
+    assert abs(r_gpu - r_orc) <= 0.002, (r_gpu, r_orc)
     assert (st[:, 5] >= 1).all()
 
 
