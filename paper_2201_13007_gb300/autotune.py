@@ -20,7 +20,8 @@ import torch
 from .index import Batch
 
 LADDER = (32, 64, 128, 256, 512, 1024, 2048)
-CANDIDATES = ((128, 11), (128, 12), (256, 12), (256, 13), (512, 13), (512, 14))
+# (threads, hash_bits); (0, 0) is the library's own choice for the bucket, so the tuner never does worse than it
+CANDIDATES = ((0, 0), (128, 11), (128, 12), (128, 14), (256, 12), (256, 13), (256, 14), (512, 13), (512, 14))
 
 
 def _key(index, k, L, M, params, ladder):
@@ -35,7 +36,7 @@ def _key(index, k, L, M, params, ladder):
 
 def tune_buckets(index, queries, k, L, M, *, ladder=LADDER, candidates=CANDIDATES, sample=2000, reps=3,
                  cache_path=None, **params):
-    """Returns a list of (L_max, threads, hash_bits), one per ladder rung."""
+    """Returns a list of (L_max, threads, hash_bits), one per ladder rung (0 = the library's choice)."""
     k = np.asarray(k, np.int32)
     L = np.asarray(L, np.int32)
     M = np.asarray(M, np.int32)
