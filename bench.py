@@ -371,6 +371,18 @@ def run_ours(args):
             single[f"{tgt}/cluster{C}"] = {"L": L, "M": M, "p50_us": float(np.percentile(lat, 50)),
                                            "p99_us": float(np.percentile(lat, 99)),
                                            "qps": 1e6 / float(np.mean(lat))}
+            try:
+                # the same 300 launches once more, untimed, with per-query counters: algorithmic bytes of
+                # a launch over its mean time, against the HBM peak
+                st1 = torch.empty((1, 8), dtype=torch.int64, device="cuda")
+                byts = 0.0
+                for i in range(300):
+                    ix32.search(q[i:i + 1], K, L, M, stream=stream, cluster=C, stats=st1)
+                    byts += algorithmic_bytes(st1.cpu().numpy(), w.R, ix32.info()["d_pad"] * 4, w.d, K, 0)
+                gbs = byts / (float(np.sum(lat)) * 1e-6) / 1e9
+                single[f"{tgt}/cluster{C}"].update({"gbs": gbs, "frac": gbs / peaks()[0]})
+            except Exception as e:  # the latency figures above stand without the byte count
+                log("single-query byte count skipped:", e)
 
     # ---- end to end through the host-buffer C call (H2D + search + D2H)
     L, M = points[head]
