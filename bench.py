@@ -467,8 +467,24 @@ def cpu_baseline(w, L, M, seconds):
     t0 = time.perf_counter()
     oracle.search(w.base, w.adj, w.entry, sample, algo="topm", L=L, K=K, M0=1, M_max=M, t=1, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": ns / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {ns} of the 10,000 queries, FP64 top-M (L={L}, M={M}), {cores} threads"}
+    out = {"value": ns / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {ns} of the 10,000 queries, FP64 top-M (L={L}, M={M}), {cores} threads"}
+    # the sequential search (Algorithm 1) beside the M-walker: per-query latency on one thread, and the
+    # sequential search's throughput on all cores, each on a small bounded sample at the same L
+    one = w.queries[:16]
+    detail = {}
+    for algo, mm in (("bfis", 1), ("topm", M)):
+        t0 = time.perf_counter()
+        oracle.search(w.base, w.adj, w.entry, one, algo=algo, L=L, K=K, M0=1, M_max=mm, t=1, nthreads=1)
+        detail[f"{algo}_one_thread_ms_per_query"] = (time.perf_counter() - t0) * 1e3 / len(one)
+    nb = int(min(w.queries.shape[0], max(64, cores * 1e3 / max(detail["bfis_one_thread_ms_per_query"], 1e-3)
+                                            * min(seconds, 4.0))))
+    t0 = time.perf_counter()
+    oracle.search(w.base, w.adj, w.entry, w.queries[:nb], algo="bfis", L=L, K=K, nthreads=cores)
+    detail["bfis_all_threads_qps"] = nb / (time.perf_counter() - t0)
+    detail["bfis_sample"] = f"first {nb} queries, FP64 BFiS (L={L}), {cores} threads; latencies on 16 queries"
+    out["detail"] = detail
+    return out
 
 
 def run_reference(args):
