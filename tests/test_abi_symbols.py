@@ -53,3 +53,40 @@ def test_argument_errors_without_gpu():
     with pytest.raises(ann.AnnError):
         _abi.ann_serve_create(None, None)
     assert "NULL" in ann.ann_last_error()
+
+
+def test_ctypes_mirrors_match_the_header_layout(tmp_path):
+    """Every struct of the header and its ctypes mirror have the same size,
+    field names, order and offsets (a C program compiled from the header
+    prints them)."""
+    from paper_2201_13007_gb300 import _abi
+    pairs = {"ann_index_info": _abi.IndexInfo, "ann_query_stats": _abi.QueryStats,
+             "ann_search_params": _abi.SearchParams, "ann_launch_info": _abi.LaunchInfo,
+             "ann_bucket_config": _abi.BucketConfig, "ann_serve_config": _abi.ServeConfig,
+             "ann_result": _abi.Result}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ann.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr  # a field missing from the header fails here
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+    # and no header field is missing from a mirror: the header's member count per struct
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ann.h")).read(), flags=re.S)
+    for cname, cls in pairs.items():
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + cname + r"\s*;", hdr).group(1)
+        members = [m for m in body.split(";") if m.strip()]
+        assert len(members) == len(cls._fields_), (cname, len(members), len(cls._fields_))
