@@ -101,7 +101,13 @@ typedef struct {
     int32_t rerank;     /* 1 = recompute the final queue's keys from FP32 rows (needs has_f32) */
     int32_t threads;    /* threads per CTA: 0 = auto; sync 64..512; async 64..1024 and >= 32*M */
     int32_t hash_bits;  /* log2 slots of the per-query visited table; 0 = auto, else 8..15 */
-    int32_t persistent; /* 1 = persistent grid that pulls queries from a device counter */
+    int32_t persistent; /* 1 = persistent grid that pulls queries from a device work counter.
+                         * The index keeps one counter per stream (up to 1024 streams per
+                         * index; more return ANN_ERR_STATE), so persistent searches on
+                         * different streams may run at the same time; calls on one stream
+                         * are ordered by the stream. A stream handle that is destroyed and
+                         * handed out again names the same counter: let the old stream's
+                         * work finish first. */
     /* Per-query settings (device int32 arrays of nq entries, or NULL for the
      * uniform k, L, M arguments). When given, k, L and M passed to the call
      * are the maxima over the batch, and each entry must lie in [1, max]. */
@@ -138,18 +144,6 @@ typedef struct {
      * not see; they only forget, which changes the number of distance
      * evaluations but never the results. */
     int32_t visited_mode;
-    /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: shared memory for
-     * staging candidate rows with bulk copies (one cp.async.bulk per row,
-     * completing on an mbarrier), instead of gathering them through
-     * registers; 0 or -1 = register gather. A query whose copies do not
-     * arrive within the kernel's wait limit gets (-1, +inf) results and
-     * stats.steps = -2. */
-    int32_t stage_bytes;
-    /* One-CTA sync kernel, FP32 / BF16 / FP16 storage: 1 = each lane streams
-     * the row chunks it reduces through a private shared-memory ring with
-     * cp.async, four groups ahead (more rows in flight per warp, no
-     * barriers); 0 = register gather. */
-    int32_t lane_pipeline;
     /* Sync kernels: 1 = the row of every vertex that passes the visited
      * filter is requested into L2 with one bulk prefetch
      * (cp.async.bulk.prefetch.L2) the moment it passes, so all of a step's
@@ -240,15 +234,16 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
 #define ANN_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* ann_search_host for callers that cannot allocate device memory when they
- * search: code running while a CUDA graph is captured on its thread (where
- * cudaMalloc is not allowed), processes whose device memory is fully held by
- * another framework's caching allocator, or latency-critical threads. The
- * paper has no counterpart; this is a deployment convenience.
+ * search: a process whose device memory is reserved up front by another
+ * framework's caching allocator (so a cudaMalloc here would fail or fragment
+ * its pool), or a latency-critical thread that must not enter the CUDA
+ * allocator, which can block on the device. The paper has no counterpart.
  *   Arguments, layout and results are those of ann_search_host (host
  *   buffers in and out, params may be NULL; the search always runs as a
- *   persistent grid). The call allocates nothing: its device scratch (the
- *   persistent grid's work counter and device copies of the queries and of
- *   the results) lives in one static device array of
+ *   persistent grid with one CTA per query). params->cluster must be 0 or 1
+ *   (ANN_ERR_ARG otherwise). The call allocates nothing: its device scratch
+ *   (the persistent grid's work counter and device copies of the queries
+ *   and of the results) lives in one static device array of
  *   ANN_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the
  *   library holds until the process exits.
  *   A batch needing more than that (256 + nq*d*4 + nq*k*12 bytes, each part
@@ -259,8 +254,8 @@ int ann_search_host(ann_index *index, const float *queries, int64_t nq, int32_t 
  *   capture.
  *   All calls share the one array, which keeps the last call's contents;
  *   calls that overlap on the GPU (other streams, other threads) race on it
- *   and must be serialised by the caller. Synchronises the stream before it
- *   returns. */
+ *   and must be serialised by the caller. Copies from and to the caller's
+ *   host buffers and synchronises the stream before it returns. */
 int ann_search_host_noalloc(const ann_index *index, const float *queries, int64_t nq, int32_t k, int32_t L,
                             int32_t M, int64_t *out_ids, float *out_dists, const ann_search_params *params,
                             void *stream);

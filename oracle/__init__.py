@@ -206,6 +206,43 @@ def exact_knn(base, queries, K, metric="l2", nthreads=1):
     return ids, keys
 
 
+def exact_knn_gemm(base, queries, K, metric="l2", chunk=256):
+    """Def. 1 through an FP64 matrix product: key = |x|^2 - 2 <q, x> (+ |q|^2)
+    for l2, -<q, x> for inner product, then the K smallest by (key, id).
+    When every coordinate is an integer the products and sums stay below
+    2^53, so every key is exact and the answer is exactly exact_knn's; on
+    other data keys differ from the direct sum only by FP64 rounding. A
+    library GEMM serves as the step that forms the dot products; everything
+    else is written out. Returns (ids int64 nq x K, keys float64 nq x K)."""
+    X = np.ascontiguousarray(base, np.float64)
+    Q = np.ascontiguousarray(queries, np.float64)
+    if Q.ndim == 1:
+        Q = Q[None, :]
+    n = X.shape[0]
+    xn = np.einsum("ij,ij->i", X, X)
+    ids = np.empty((Q.shape[0], K), np.int64)
+    keys = np.empty((Q.shape[0], K), np.float64)
+    for a in range(0, Q.shape[0], chunk):
+        q = Q[a:a + chunk]
+        dot = q @ X.T
+        if metric == "l2":
+            D = xn[None, :] - 2.0 * dot + np.einsum("ij,ij->i", q, q)[:, None]
+        else:
+            D = -dot
+        kk = min(K, n)
+        part = np.argpartition(D, kk - 1, axis=1)[:, :kk]
+        for r in range(q.shape[0]):
+            kth = D[r, part[r]].max()
+            cand = np.flatnonzero(D[r] <= kth)          # every id tied with the K-th key takes part
+            o = np.lexsort((cand, D[r, cand]))[:kk]
+            ids[a + r, :kk] = cand[o]
+            keys[a + r, :kk] = D[r, cand[o]]
+        if kk < K:
+            ids[a:a + chunk, kk:] = -1
+            keys[a:a + chunk, kk:] = np.inf
+    return ids, keys
+
+
 def rerank(base32, queries, cand, K, metric="l2"):
     """Recompute candidate keys from FP32 rows, sort by (key, id), keep K."""
     base32 = _f32(base32)

@@ -51,8 +51,7 @@ class SearchParams(ctypes.Structure):
                 ("k_per_query", ctypes.c_void_p), ("L_per_query", ctypes.c_void_p),
                 ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p),
                 ("order", ctypes.c_void_p), ("cluster", ctypes.c_int32), ("phase_cycles", ctypes.c_void_p),
-                ("visited_mode", ctypes.c_int32), ("stage_bytes", ctypes.c_int32),
-                ("lane_pipeline", ctypes.c_int32), ("l2_prefetch", ctypes.c_int32),
+                ("visited_mode", ctypes.c_int32), ("l2_prefetch", ctypes.c_int32),
                 ("team_lanes", ctypes.c_int32)]
 
 

@@ -6,11 +6,16 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 
 #include "ann_internal.cuh"
 
 struct ann_index {
     ann::IndexData d;
+    // stream -> work-counter slot (see IndexData::work_counter)
+    std::mutex slot_mu;
+    std::unordered_map<std::string, int> slot_of;
 };
 
 namespace {
@@ -105,7 +110,9 @@ int create_impl(const float *base, int64_t n, int32_t d, int32_t storage, const 
     const size_t base_bytes = (size_t)n * x.d_pad * es;
     if ((e = cudaMalloc(&x.base, base_bytes)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(base)"));
     if ((e = cudaMalloc(&x.adj, (size_t)n * R * 4)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(adj)"));
-    if ((e = cudaMalloc(&x.work_counter, 64)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(counter)"));
+    if ((e = cudaMalloc(&x.work_counter, (size_t)ann::kCounterSlots * ann::kCounterStride * sizeof(int))) !=
+        cudaSuccess)
+        return cleanup_fail(cuda_fail(e, "cudaMalloc(counters)"));
     x.device_bytes = base_bytes + (size_t)n * R * 4;
     if (storage == ANN_STORE_E4M3) {
         if ((e = cudaMalloc(&x.scales, (size_t)n * 4)) != cudaSuccess) return cleanup_fail(cuda_fail(e, "cudaMalloc(scales)"));
@@ -290,19 +297,6 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         a.team_lanes = log2_team(x.d_pad * ann::storage_bytes(x.storage) / 16);
         a.team_lanes32 = log2_team(x.d_pad32 * 4 / 16);
     }
-    if (p->stage_bytes < -1) return fail(ANN_ERR_ARG, "stage_bytes=%d must be -1, 0 or positive", p->stage_bytes);
-    if (p->lane_pipeline && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
-        // per lane: 4 groups of 2 rows of its team in flight (compute_keys_pipe<.., U = 2, D = 4>)
-        const int es = ann::storage_bytes(x.storage);
-        const int cpr = x.d_pad * es / 16;
-        int ts = 1;
-        while (ts < cpr && ts < 32) ts <<= 1;
-        a.pipe_bytes = (threads / 32) * 4 * 2 * (32 / ts) * x.d_pad * es;
-    } else if (p->stage_bytes > 0 && !async && csize == 1 && x.storage != ANN_STORE_E4M3) {
-        const int row_bytes = x.d_pad * ann::storage_bytes(x.storage);
-        a.tma_rows = p->stage_bytes / row_bytes;
-        if (a.tma_rows < 1) a.tma_rows = 1;
-    }
     a.out_ids = out_ids;
     a.out_dists = out_dists;
     a.stats = p->stats;
@@ -313,20 +307,24 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.Lcap = L;
     int need = M * x.R;
     if (a.rerank && L > need) need = L;
+    if (!async && csize == 1) {  // the warps' fresh-id lists live in the candidate segment (two ids per entry)
+        const int nw = threads / 32;
+        const int fresh_entries = (nw * ((M + nw - 1) / nw) * x.R + 1) / 2;
+        if (fresh_entries > need) need = fresh_entries;
+    }
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
     a.qfloats = x.d_pad > x.d_pad32 ? x.d_pad : x.d_pad32;
     auto smem_for = [&](int bits) {
         if (csize > 1) return ann::cluster_smem_size(a.qfloats, a.Lcap, a.Ccap, bits, M);
         return async ? ann::async_smem_size(a.qfloats, a.Lcap, threads / 32, bits)
-                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M,
-                                        a.tma_rows * x.d_pad * ann::storage_bytes(x.storage) + a.pipe_bytes,
-                                        slot_bytes_for(bits)).total;
+                     : ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, bits, M, slot_bytes_for(bits), threads / 32).total;
     };
     int smem = smem_for(a.hash_bits);
     // an automatic visited table shrinks until the layout fits (it may then forget more often)
     while (p->hash_bits == 0 && smem > max_dyn_smem() && a.hash_bits > 10) smem = smem_for(--a.hash_bits);
     a.slot_bytes = slot_bytes_for(a.hash_bits);
     a.tag_bits = a.slot_bytes < 4 && idbits > a.hash_bits ? idbits - a.hash_bits : 0;
+    a.sync_lay = ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M, a.slot_bytes, threads / 32);
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
                     smem, max_dyn_smem());
@@ -340,7 +338,7 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (a.persistent && csize == 1 && nq > 0) {
         int bps = 0;
         cudaError_t e = async ? ann::async_search_occupancy(x.storage, threads, smem, &bps)
-                              : ann::sync_search_occupancy(x.storage, threads, smem, &bps);
+                              : ann::sync_search_occupancy(x.storage, x.metric, threads, smem, &bps);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         if (bps < 1) return fail(ANN_ERR_ARG, "kernel does not fit on an SM");
         int64_t g = (int64_t)bps * sm_count();
@@ -366,12 +364,46 @@ namespace {
 using ann::Plan;
 using ann::plan_search;
 
-int launch_plan(const ann_index *index, const Plan &plan, cudaStream_t s) {
-    if (plan.a.nq == 0) return ANN_OK;
+// The work-counter slot of a stream. Work on one stream runs in order, so a
+// stream can reuse its slot call after call; different streams get different
+// slots. The per-thread default stream is one stream per host thread, so it
+// is keyed by the thread as well.
+int counter_slot(const ann_index *index, cudaStream_t s, int **out) {
+    ann_index *ix = const_cast<ann_index *>(index);
+    std::string key = std::to_string(reinterpret_cast<uintptr_t>(s));
+    if (s == cudaStreamPerThread) {
+        key += "/";
+        key += std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id()));
+    } else if (s == cudaStreamLegacy) {
+        key = "0";  // the legacy default stream, however it is named
+    }
+    std::lock_guard<std::mutex> lock(ix->slot_mu);
+    auto it = ix->slot_of.find(key);
+    int slot;
+    if (it != ix->slot_of.end()) {
+        slot = it->second;
+    } else {
+        if ((int)ix->slot_of.size() >= ann::kCounterSlots)
+            return fail(ANN_ERR_STATE, "more than %d streams ran persistent searches on this index",
+                        ann::kCounterSlots);
+        slot = (int)ix->slot_of.size();
+        ix->slot_of.emplace(key, slot);
+    }
+    *out = index->d.work_counter + (size_t)slot * ann::kCounterStride;
+    return ANN_OK;
+}
+
+int launch_plan(const ann_index *index, const Plan &plan_in, cudaStream_t s) {
+    if (plan_in.a.nq == 0) return ANN_OK;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != index->d.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, index->d.device);
-    if (plan.a.persistent) ANN_CUDA(cudaMemsetAsync(index->d.work_counter, 0, sizeof(int), s));
+    Plan plan = plan_in;
+    if (plan.a.persistent) {
+        int rc = counter_slot(index, s, &plan.a.work_counter);
+        if (rc != ANN_OK) return rc;
+        ANN_CUDA(cudaMemsetAsync(plan.a.work_counter, 0, sizeof(int), s));
+    }
     cudaError_t e = ann::launch(plan, s);
     if (e != cudaSuccess) return cuda_fail(e, "search launch");
     return ANN_OK;
@@ -486,14 +518,13 @@ const char *ann_last_error(void) { return g_err.c_str(); }
 // ------------------------------------------------------------------------
 // Allocation-free host-buffer search.
 //
-// For callers that must not allocate device memory at search time: code that
-// runs while a CUDA graph is being captured on its thread (cudaMalloc is not
-// allowed there), processes whose device memory is fully reserved by another
-// framework's caching allocator, or latency-critical threads that cannot
-// afford an allocator call. This entry point keeps all of its device scratch
-// (the persistent grid's work counter and the staging copies of the queries
-// and results) in one file-scope static device array, and calls no
-// cudaMalloc, cudaFree or other allocating routine.
+// For callers that must not allocate device memory at search time: processes
+// whose device memory is reserved up front by another framework's caching
+// allocator, or latency-critical threads that must not enter the CUDA
+// allocator (it can block on the device). This entry point keeps all of its
+// device scratch (the persistent grid's work counter and the staging copies
+// of the queries and results) in one file-scope static device array, and
+// calls no cudaMalloc, cudaFree or other allocating routine.
 namespace {
 
 constexpr size_t kNoallocScratchBytes = (size_t)ANN_NOALLOC_SCRATCH_BYTES;
@@ -537,6 +568,9 @@ extern "C" int ann_search_host_noalloc(const ann_index *index, const float *quer
     memset(&p, 0, sizeof(p));
     if (params) p = *params;
     p.persistent = 1;
+    if (p.cluster > 1)
+        return fail(ANN_ERR_ARG, "cluster=%d: the allocation-free search runs one CTA per query (0 or 1)",
+                    p.cluster);
     Plan plan;
     int rc = plan_search(index, reinterpret_cast<const float *>(16), nq, k, L, M,
                          reinterpret_cast<int64_t *>(16), reinterpret_cast<float *>(16), &p, &plan);
@@ -569,9 +603,7 @@ extern "C" int ann_search_host_noalloc(const ann_index *index, const float *quer
     // the array keeps the previous call's contents: the counter must start at zero
     ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
     ANN_CUDA(cudaMemcpyAsync(dq, queries, qb, cudaMemcpyHostToDevice, s));
-    cudaError_t e = plan.mode == ANN_MODE_ASYNC
-                        ? ann::launch_async_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s)
-                        : ann::launch_sync_search(plan.a, plan.storage, plan.threads, plan.smem, plan.grid, s);
+    cudaError_t e = ann::launch(plan, s);
     if (e != cudaSuccess) return cuda_fail(e, "search launch");
     ANN_CUDA(cudaMemcpyAsync(out_ids, dids, ib, cudaMemcpyDeviceToHost, s));
     ANN_CUDA(cudaMemcpyAsync(out_dists, ddist, db, cudaMemcpyDeviceToHost, s));

@@ -33,9 +33,40 @@ struct IndexData {
     // staging for ann_search_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
-    // device counter for the persistent grid
+    // device work counters of persistent grids: one slot (its own 128-byte line) per stream that
+    // searches the index, so persistent searches on different streams never share a counter
     int *work_counter = nullptr;
 };
+
+static constexpr int kCounterSlots = 1024;
+static constexpr int kCounterStride = 32;  // ints between slots (one 128-byte line each)
+
+// Byte offsets of the dynamic shared-memory segments (16-byte aligned).
+struct SmemLayout {
+    int q_off, q0_off, q1_off, cand_off, cand2_off, dup_off, hash_off, act_off, total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+// Shared memory of the one-CTA sync kernel with nw warps. The cand segment
+// holds each warp's fresh ids during a step (nw * ceil(Mcap / nw) * R uint32,
+// which the host guarantees fit in Ccap entries) and sort output after it;
+// act holds each warp's selected vertices and their queue positions.
+__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
+                                                  int slot_bytes, int nw) {
+    SmemLayout s;
+    int o = 0;
+    s.q_off = o;    o += align16(qfloats * 4);
+    s.q0_off = o;   o += align16(Lcap * 8);
+    s.q1_off = o;   o += align16(Lcap * 8);
+    s.cand_off = o; o += align16(Ccap * 8);
+    s.cand2_off = o; o += align16(Ccap * 8);
+    s.dup_off = o;  o += align16(Ccap);
+    s.hash_off = o; o += align16((1 << hash_bits) * slot_bytes);
+    s.act_off = o;  o += align16(2 * nw * ((Mcap + nw - 1) / nw) * 4);
+    s.total = o;
+    return s;
+}
 
 // Everything a search launch needs, passed by value.
 struct SearchArgs {
@@ -58,8 +89,6 @@ struct SearchArgs {
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
     int32_t slot_bytes;    // direct-mapped slot: 4 = a full id; 1 or 2 = a tag (the hashed id's bits below the index)
     int32_t tag_bits;      // bits of the tag when slot_bytes < 4
-    int32_t tma_rows;      // rows per bulk-copy staging batch (0 = gather rows through registers)
-    int32_t pipe_bytes;    // per-CTA ring of the per-lane cp.async pipeline (0 = off)
     int32_t l2_prefetch;   // 1 = bulk L2 prefetch of each candidate row once it passes the visited filter
     int32_t team_lanes;    // distance gather: log2 of the lanes that share one candidate row
     int32_t team_lanes32;  // the same for the FP32 rows of the re-rank
@@ -74,32 +103,8 @@ struct SearchArgs {
     int32_t Lcap;        // queue capacity
     int32_t Ccap;        // candidate / sort buffer, power of two >= 32
     int32_t qfloats;     // query buffer length
+    SmemLayout sync_lay; // one-CTA sync kernel: segment offsets (kernel parameters, so no register holds them)
 };
-
-// Byte offsets of the dynamic shared-memory segments (16-byte aligned).
-struct SmemLayout {
-    int q_off, q0_off, q1_off, cand_off, cand2_off, dup_off, hash_off, act_off, bar_off, stage_off, total;
-};
-
-__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
-
-__host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
-                                                  int stage_bytes = 0, int slot_bytes = 4) {
-    SmemLayout s;
-    int o = 0;
-    s.q_off = o;    o += align16(qfloats * 4);
-    s.q0_off = o;   o += align16(Lcap * 8);
-    s.q1_off = o;   o += align16(Lcap * 8);
-    s.cand_off = o; o += align16(Ccap * 8);
-    s.cand2_off = o; o += align16(Ccap * 8);
-    s.dup_off = o;  o += align16(Ccap);
-    s.hash_off = o; o += align16((1 << hash_bits) * slot_bytes);
-    s.act_off = o;  o += align16(Mcap * 4);
-    s.bar_off = o;  o += 16;
-    s.stage_off = o; o += align16(stage_bytes);
-    s.total = o;
-    return s;
-}
 
 inline int next_pow2(int x) {
     int p = 1;
@@ -120,7 +125,7 @@ inline int storage_bytes(int storage) {
 // kernels/launchers (search_sync.cu)
 cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, int smem_bytes,
                                int grid, cudaStream_t stream);
-cudaError_t sync_search_occupancy(int storage, int threads, int smem_bytes, int *blocks_per_sm);
+cudaError_t sync_search_occupancy(int storage, int metric, int threads, int smem_bytes, int *blocks_per_sm);
 
 // search_async.cu
 cudaError_t launch_async_search(const SearchArgs &a, int storage, int threads, int smem_bytes, int grid,

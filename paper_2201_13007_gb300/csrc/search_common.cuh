@@ -143,11 +143,10 @@ __device__ __forceinline__ uint4 ld_row_chunk(const uint4 *p) {
 // All warps of the block take part. With out == nullptr the packed entries
 // are written back in place; otherwise only entries below `limit` (in
 // (key, id) order) are appended to out[] through the shared counter *out_n.
-template <int STORE, int NT, int U = 2>
-__device__ __forceinline__ void compute_keys(const void *rows, const float *scales, int row_elems,
-                                             int metric, const float *qv, entry_t *cand, int nc,
-                                             entry_t limit = kEmptyEntry, entry_t *out = nullptr,
-                                             int *out_n = nullptr) {
+template <int STORE, int NT, bool L2, int U = 2>
+__device__ __forceinline__ void compute_keys_m(const void *rows, const float *scales, int row_elems,
+                                               const float *qv, entry_t *cand, int nc, entry_t limit,
+                                               entry_t *out, int *out_n) {
     constexpr int NW = NT / 32;
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -157,7 +156,7 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
     const int rpw = 32 / ts;
     const int team = lane / ts, tl = lane & (ts - 1);
     const int iters = (cpr + ts - 1) / ts;
-    const bool l2 = metric == ANN_METRIC_L2;
+    constexpr bool l2 = L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
     for (int c0 = warp * rpw * U; c0 < nc; c0 += NW * rpw * U) {
         float2 acc[U];
@@ -203,23 +202,37 @@ __device__ __forceinline__ void compute_keys(const void *rows, const float *scal
     }
 }
 
+// The metric is a template parameter of the loop bodies, so only one
+// distance formula is compiled into each: a runtime test inside the chunk
+// math would be if-converted into both formulas.
+template <int STORE, int NT, int U = 2>
+__device__ __forceinline__ void compute_keys(const void *rows, const float *scales, int row_elems,
+                                             int metric, const float *qv, entry_t *cand, int nc,
+                                             entry_t limit = kEmptyEntry, entry_t *out = nullptr,
+                                             int *out_n = nullptr) {
+    if (metric == ANN_METRIC_L2)
+        compute_keys_m<STORE, NT, true, U>(rows, scales, row_elems, qv, cand, nc, limit, out, out_n);
+    else
+        compute_keys_m<STORE, NT, false, U>(rows, scales, row_elems, qv, cand, nc, limit, out, out_n);
+}
+
 // Same contract as the filtered compute_keys, with teams of ts lanes (a
 // power of two, 1..32) per row and each lane walking its own chunks of the
 // row (chunk tl, tl + ts, ...), G of them in flight per round. A warp covers
 // 32 / ts rows at once, so the shuffle reduction (log2 ts levels) and the
 // append are paid once per 32 / ts rows; with small teams that is far fewer
 // instructions per row than one chunk per lane.
-template <int STORE, int NT, int G = 2>
-__device__ __forceinline__ void compute_keys_teams(const void *rows, const float *scales, int row_elems, int metric,
-                                                   const float *qv, const entry_t *cand, int nc, int lts,
-                                                   entry_t limit, entry_t *out, int *out_n) {
+template <int STORE, int NT, bool L2, int G>
+__device__ __forceinline__ void compute_keys_teams_m(const void *rows, const float *scales, int row_elems,
+                                                     const float *qv, const entry_t *cand, int nc, int lts,
+                                                     entry_t limit, entry_t *out, int *out_n) {
     constexpr int NW = NT / 32;
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ts = 1 << lts, rpw = 32 >> lts;
     const int cpr = row_elems / EPC;
     const int team = lane >> lts, tl = lane & (ts - 1);
-    const bool l2 = metric == ANN_METRIC_L2;
+    constexpr bool l2 = L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
     for (int c0 = warp * rpw; c0 < nc; c0 += NW * rpw) {
         const int c = c0 + team;
@@ -249,6 +262,16 @@ __device__ __forceinline__ void compute_keys_teams(const void *rows, const float
         base = __shfl_sync(kFull, base, 0);
         if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
     }
+}
+
+template <int STORE, int NT, int G = 2>
+__device__ __forceinline__ void compute_keys_teams(const void *rows, const float *scales, int row_elems, int metric,
+                                                   const float *qv, const entry_t *cand, int nc, int lts,
+                                                   entry_t limit, entry_t *out, int *out_n) {
+    if (metric == ANN_METRIC_L2)
+        compute_keys_teams_m<STORE, NT, true, G>(rows, scales, row_elems, qv, cand, nc, lts, limit, out, out_n);
+    else
+        compute_keys_teams_m<STORE, NT, false, G>(rows, scales, row_elems, qv, cand, nc, lts, limit, out, out_n);
 }
 
 // ------------------------------------------------------------- visited set
@@ -387,9 +410,9 @@ namespace ann {
 // Warp-level key computation for the nc <= 32 candidates whose ids sit in the
 // low word of c[0..nc) (a per-warp shared buffer); results are written back
 // packed. Same team layout as compute_keys, one warp only.
-template <int STORE, int U = 4>
-__device__ __forceinline__ void warp_compute_keys(const void *rows, const float *scales, int row_elems,
-                                                  int metric, const float *qv, entry_t *c, int nc) {
+template <int STORE, bool L2, int U>
+__device__ __forceinline__ void warp_compute_keys_m(const void *rows, const float *scales, int row_elems,
+                                                    const float *qv, entry_t *c, int nc) {
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31;
     const int cpr = row_elems / EPC;
@@ -398,7 +421,7 @@ __device__ __forceinline__ void warp_compute_keys(const void *rows, const float 
     const int rpw = 32 / ts;
     const int team = lane / ts, tl = lane & (ts - 1);
     const int iters = (cpr + ts - 1) / ts;
-    const bool l2 = metric == ANN_METRIC_L2;
+    constexpr bool l2 = L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
     for (int c0 = 0; c0 < nc; c0 += rpw * U) {
         float2 acc[U];
@@ -432,6 +455,15 @@ __device__ __forceinline__ void warp_compute_keys(const void *rows, const float 
         }
     }
     __syncwarp();
+}
+
+template <int STORE, int U = 4>
+__device__ __forceinline__ void warp_compute_keys(const void *rows, const float *scales, int row_elems,
+                                                  int metric, const float *qv, entry_t *c, int nc) {
+    if (metric == ANN_METRIC_L2)
+        warp_compute_keys_m<STORE, true, U>(rows, scales, row_elems, qv, c, nc);
+    else
+        warp_compute_keys_m<STORE, false, U>(rows, scales, row_elems, qv, c, nc);
 }
 
 // Ascending sort of the 32 entries held one per lane.
@@ -603,210 +635,6 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
     }
     __syncthreads();
     return min(L, qlen + ncl);
-}
-
-}  // namespace ann
-
-namespace ann {
-
-}  // namespace ann
-
-namespace ann {
-
-// ------------------------------------------------------------- TMA staging
-// One-dimensional bulk copies (cp.async.bulk) of whole rows into shared
-// memory, completing on an mbarrier with a transaction count. A copy moves a
-// row with a single instruction and holds no registers while in flight, so a
-// CTA can keep as many rows in flight as its staging area holds.
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bounded wait on the phase with the given parity; returns false if the
-// phase did not complete within the iteration limit.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int max_iters) {
-    for (int i = 0; i < max_iters; ++i) {
-        unsigned done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void bulk_row_to_smem(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Keys of the nc candidates in cand[] (ids in the low word), rows fetched by
-// bulk copies in batches of up to stage_rows rows; survivors below `limit`
-// are appended to out[] through *out_n (as compute_keys does). *parity is the
-// mbarrier phase to wait for next and is advanced per batch. Returns false
-// (identically in every thread) if a batch did not arrive within the wait
-// limit. Every thread must call it; it ends with a __syncthreads().
-template <int STORE, int NT>
-__device__ bool compute_keys_tma(const void *rows, int row_elems, int metric, const float *qv, const entry_t *cand,
-                                 int nc, unsigned char *stage, int stage_rows, unsigned long long *bar,
-                                 unsigned *parity, entry_t limit, entry_t *out, int *out_n) {
-    constexpr int NW = NT / 32;
-    constexpr int EPC = Chunk<STORE>::kElems;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cpr = row_elems / EPC;
-    const int row_bytes = cpr * 16;
-    int ts = 1;
-    while (ts < cpr && ts < 32) ts <<= 1;
-    const int rpw = 32 / ts;
-    const int team = lane / ts, tl = lane & (ts - 1);
-    const int iters = (cpr + ts - 1) / ts;
-    const bool l2 = metric == ANN_METRIC_L2;
-    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
-    for (int b0 = 0; b0 < nc; b0 += stage_rows) {
-        const int nb = min(stage_rows, nc - b0);
-        if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(nb * row_bytes));
-        __syncthreads();
-        for (int r = tid; r < nb; r += NT) {
-            const uint32_t id = (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull);
-            bulk_row_to_smem(stage + (size_t)r * row_bytes, g + (size_t)id * row_bytes, (unsigned)row_bytes, bar);
-        }
-        const bool ok = mbar_wait(bar, *parity, 1 << 22);
-        *parity ^= 1u;
-        if (__syncthreads_or(!ok)) return false;
-        for (int c0 = warp * rpw; c0 < nb; c0 += NW * rpw) {
-            const int r = c0 + team;
-            const bool valid = r < nb;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int it = 0; it < iters; ++it) {
-                const int ch = tl + it * ts;
-                if (valid && ch < cpr) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(stage + (size_t)r * row_bytes + ch * 16);
-                    Chunk<STORE>::add(acc, v, qv + ch * EPC, 1.f, l2);
-                }
-            }
-            float s = acc.x + acc.y;
-            for (int off = ts >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
-            const uint32_t id = valid ? (uint32_t)(cand[b0 + r] & 0xFFFFFFFFull) : 0u;
-            const entry_t e = pack_entry(l2 ? s : -s, id);
-            const bool keep = tl == 0 && valid && e < limit;
-            const unsigned bal = __ballot_sync(kFull, keep);
-            int base = 0;
-            if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
-            base = __shfl_sync(kFull, base, 0);
-            if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
-        }
-        __syncthreads();
-        fence_proxy_async_smem();  // the stage's generic reads finish before the next bulk writes
-    }
-    return true;
-}
-
-}  // namespace ann
-
-namespace ann {
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// compute_keys (filtered form) with each lane's row chunks streamed through
-// a private shared-memory ring by cp.async: a lane copies exactly the chunks
-// it later reduces, D groups of U rows per team ahead, so rows stay in flight
-// without holding registers and without any barrier between lanes or warps.
-// ring: this CTA's staging area, (NT/32) * D * U * rpw * row_bytes bytes.
-template <int STORE, int NT, int U = 2, int D = 4>
-__device__ __forceinline__ void compute_keys_pipe(const void *rows, const float *scales, int row_elems, int metric,
-                                                  const float *qv, const entry_t *cand, int nc, unsigned char *ring,
-                                                  entry_t limit, entry_t *out, int *out_n) {
-    constexpr int NW = NT / 32;
-    constexpr int EPC = Chunk<STORE>::kElems;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cpr = row_elems / EPC;
-    const int row_bytes = cpr * 16;
-    int ts = 1;
-    while (ts < cpr && ts < 32) ts <<= 1;
-    const int rpw = 32 / ts;
-    const int team = lane / ts, tl = lane & (ts - 1);
-    const int iters = (cpr + ts - 1) / ts;
-    const bool l2 = metric == ANN_METRIC_L2;
-    const unsigned char *g = reinterpret_cast<const unsigned char *>(rows);
-    unsigned char *wring = ring + (size_t)warp * D * U * rpw * row_bytes;
-    const int per = NW * rpw * U;                 // rows per group over the whole CTA
-    const int first = warp * rpw * U;
-    const int ngroups = first < nc ? (nc - first + per - 1) / per : 0;  // warp-uniform
-    auto slot = [&](int k, int u) { return wring + ((size_t)((k % D) * U + u) * rpw + team) * row_bytes; };
-    auto issue = [&](int k) {
-        if (k < ngroups) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int c = first + k * per + u * rpw + team;
-                if (c < nc) {
-                    const uint32_t id = (uint32_t)(cand[c] & 0xFFFFFFFFull);
-                    const unsigned char *src = g + (size_t)id * row_bytes;
-                    unsigned char *dst = slot(k, u);
-                    for (int it = 0; it < iters; ++it) {
-                        const int ch = tl + it * ts;
-                        if (ch < cpr) cp_async16(dst + ch * 16, src + ch * 16);
-                    }
-                }
-            }
-        }
-        cp_async_commit();  // one group per step of the pipeline, possibly empty
-    };
-#pragma unroll
-    for (int k = 0; k < D - 1; ++k) issue(k);
-    for (int k = 0; k < ngroups; ++k) {
-        issue(k + D - 1);
-        cp_async_wait<D - 1>();  // this lane's copies of group k have landed
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = first + k * per + u * rpw + team;
-            const bool valid = c < nc;
-            float2 acc = make_float2(0.f, 0.f);
-            uint32_t id = 0;
-            float sc = 1.f;
-            if (valid) {
-                id = (uint32_t)(cand[c] & 0xFFFFFFFFull);
-                if (STORE == ANN_STORE_E4M3) sc = __ldg(scales + id);
-                const unsigned char *src = slot(k, u);
-                for (int it = 0; it < iters; ++it) {
-                    const int ch = tl + it * ts;
-                    if (ch < cpr) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(src + ch * 16);
-                        Chunk<STORE>::add(acc, v, qv + ch * EPC, sc, l2);
-                    }
-                }
-            }
-            float s = acc.x + acc.y;
-            for (int off = ts >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
-            const entry_t e = pack_entry(l2 ? s : -s, id);
-            const bool keep = tl == 0 && valid && e < limit;
-            const unsigned bal = __ballot_sync(kFull, keep);
-            int base = 0;
-            if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
-            base = __shfl_sync(kFull, base, 0);
-            if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
-        }
-    }
-    cp_async_wait<0>();
 }
 
 }  // namespace ann

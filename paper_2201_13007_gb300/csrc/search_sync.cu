@@ -2,41 +2,48 @@
 //
 // Follows Algorithm 1 (BFiS) generalised by Sec. 4.1 to expand the top-M
 // unchecked candidates per step, with the Sec. 4.2 staged schedule (M starts
-// at M0 and doubles every t steps up to M_max). Every step is a CTA barrier,
-// so the result is deterministic: it is the same top-L queue the sequential
-// definition produces, whatever order the warps touch it in.
+// at M0 and doubles every t steps up to M_max). Every step ends in CTA
+// barriers, so the result is deterministic: it is the same top-L queue the
+// sequential definition produces, whatever order the warps touch it in.
 //
-// Per step, inside one CTA:
-//   select   warp 0 takes the first min(M_s, #unchecked) unchecked entries of
-//            the sorted queue by ballot + popc and marks them checked;
-//   expand   all threads read the M adjacency rows (coalesced int32 rows) and
-//            insert each neighbour into the shared-memory visited table;
-//            survivors get a slot in the candidate buffer (warp-aggregated
-//            atomics);
-//   distance teams of lanes gather the candidates' rows with 16-byte
-//            non-caching loads and reduce partial sums with shuffles;
-//   sort     bitonic sort of the packed (key, id) candidates;
-//   merge    drop candidates whose id is already queued (only possible after
-//            the visited table forgot a vertex), then a rank-based parallel
-//            merge of the queue and the candidates, truncated to L.
-// The visited table is reset to the queue's ids when it is half full; the
-// queue is then still the top-L of everything seen (a forgotten vertex that
-// is met again either duplicates a queued id, which the merge drops, or ranks
-// below the L-th entry again), so ids are unchanged and only the distance
-// count grows.
+// One step, inside one CTA of NW warps:
+//   select   every warp reads the (stable) sorted queue and computes the same
+//            first min(M_s, #unchecked) unchecked entries by ballot + popc;
+//            the selected vertex of rank r is expanded by warp r mod NW, so no
+//            warp waits for another to publish the selection;
+//   expand   each warp reads the adjacency rows of its own selected vertices
+//            (one lane per slot, coalesced int32 rows), inserts each
+//            neighbour into the shared visited set and appends the fresh ones
+//            to its own list (one warp scan per batch of rows), asking L2 for
+//            each fresh row as it goes;
+//   distance each warp gathers its own fresh rows with teams of lanes (16-byte
+//            non-caching loads, shuffle reduction) and appends every
+//            candidate below the queue's L-th entry to the CTA's survivor
+//            list. One barrier; then each warp marks its selected entries
+//            checked (deferred so that no warp's select scan saw a mark);
+//   sort     the survivors by (key, id): warp sort, run-rank sort or bitonic;
+//   merge    drop survivors whose id is already queued (only possible once
+//            the visited set forgot a vertex), then a merge-path merge of the
+//            queue and the survivors, truncated to L.
+// The visited set may forget vertices (a direct-mapped cache evicts, an
+// open-addressing table is reset to the queued ids when half full); the queue
+// is then still the top-L of everything seen (a forgotten vertex that is met
+// again either duplicates a queued id, which the merge drops, or ranks below
+// the L-th entry again), so ids are unchanged and only the distance count
+// grows.
 #include "search_common.cuh"
 
 namespace ann {
 
 struct Ctrl {
-    int nact;
-    int ncand;
-    int qlen;
+    int ns[2];     // survivors appended in the step of this parity
     int hash_count;
+    int do_reset;  // open addressing: the table is half full, reset it before the next select
     int anydup;
-    int ns;      // candidates that beat the L-th queued entry this step
-    int unsafe;  // 1 once the visited table may have forgotten a vertex this query
-    int qi;
+    int unsafe;    // 1 once the visited set may have forgotten a vertex this query
+    int first_un;  // every queue entry before this position is checked
+    int qi, k, L, Mmax;  // the query and its settings (kept here, not in registers, across the step loop)
+    int wevals;    // fresh vertices of this query, summed per warp and step
     // per-query counters, updated by thread 0 only
     long long steps, expansions, evals, resets, dropped, t0;
     long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
@@ -52,21 +59,61 @@ __device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, u
     return visited_exchange(table, a.hash_bits, id);
 }
 
-template <int NT, int STORE>
+// Keys of the nf rows whose ids are in ids[0..nf) (one warp), by teams of
+// 2^lts lanes per row; each lane walks its own 16-byte chunks of the row, G
+// of them in flight. Candidates below `limit` are appended to out[] through
+// the shared counter *out_n. Returns nothing; no barrier.
+template <int STORE, int G, bool L2>
+__device__ __forceinline__ void warp_keys_append_m(const void *rows, const float *scales, uint32_t cpr,
+                                                   const float *qv, const uint32_t *ids, int nf, int lts,
+                                                   entry_t limit, entry_t *out, int *out_n) {
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int lane = threadIdx.x & 31;
+    const int ts = 1 << lts, rpw = 32 >> lts;
+    const int team = lane >> lts, tl = lane & (ts - 1);
+    constexpr bool l2 = L2;
+    const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
+    for (int c0 = 0; c0 < nf; c0 += rpw) {
+        const int c = c0 + team;
+        const bool valid = c < nf;
+        const uint32_t id = valid ? ids[c] : 0u;
+        const float sc = (STORE == ANN_STORE_E4M3 && valid) ? __ldg(scales + id) : 1.f;
+        const uint4 *rp = rbase + (size_t)id * cpr;
+        float2 acc = make_float2(0.f, 0.f);
+        if (valid) {
+            for (uint32_t ch0 = tl; ch0 < cpr; ch0 += ts * G) {
+                uint4 v[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) v[g] = ld_row_chunk(rp + ch0 + g * ts);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) Chunk<STORE>::add(acc, v[g], qv + (ch0 + g * ts) * EPC, sc, l2);
+            }
+        }
+        float r = acc.x + acc.y;
+        for (int off = ts >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+        const entry_t e = pack_entry(l2 ? r : -r, id);
+        const bool keep = tl == 0 && valid && e < limit;
+        const unsigned bal = __ballot_sync(kFull, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
+    }
+}
+
+template <int NT, int STORE, bool L2>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(const SearchArgs a) {
+    constexpr int NW = NT / 32;
+    constexpr uint32_t ES = STORE == ANN_STORE_F32 ? 4u : STORE == ANN_STORE_E4M3 ? 1u : 2u;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int row_bytes = a.d_pad * (STORE == ANN_STORE_F32 ? 4 : STORE == ANN_STORE_E4M3 ? 1 : 2);
-    const SmemLayout lay = sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M,
-                                       a.tma_rows * row_bytes + a.pipe_bytes, a.slot_bytes);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + lay.bar_off);
-    unsigned char *stage = smem + lay.stage_off;
-    unsigned parity = 0;
-    if (a.tma_rows > 0) {
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-    }
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t row_bytes = (uint32_t)a.d_pad * ES;
+    const uint32_t cpr = row_bytes / 16u;
+    const SmemLayout &lay = a.sync_lay;
     float *qv = reinterpret_cast<float *>(smem + lay.q_off);
     entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
     entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
@@ -74,28 +121,39 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     entry_t *surv = reinterpret_cast<entry_t *>(smem + lay.cand2_off);
     unsigned char *dup = smem + lay.dup_off;
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
-    int *act = reinterpret_cast<int *>(smem + lay.act_off);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
+    const int SR = (R + 31) >> 5;                 // 32-lane parts per adjacency row
+    const int rows_w = (a.M + NW - 1) / NW;      // most rows one warp expands in a step
+    // this warp's selected vertices (ids, queue positions) and its fresh ids
+    int *sel_id = reinterpret_cast<int *>(smem + lay.act_off) + warp * rows_w;
+    int *sel_pos = reinterpret_cast<int *>(smem + lay.act_off) + NW * rows_w + warp * rows_w;
+    uint32_t *fresh = reinterpret_cast<uint32_t *>(cand) + (size_t)warp * rows_w * R;
 
     for (;;) {
         if (tid == 0) {
             const int item = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
-            ctl.qi = item >= a.nq ? -1 : (a.order ? a.order[item] : item);
+            const int q = item >= a.nq ? -1 : (a.order ? a.order[item] : item);
+            ctl.qi = q;
+            if (q >= 0) {
+                ctl.k = a.k_arr ? a.k_arr[q] : a.k;
+                ctl.L = a.L_arr ? a.L_arr[q] : a.L;
+                ctl.Mmax = a.M_arr ? a.M_arr[q] : a.M;
+            }
+            ctl.wevals = 0;
             ctl.t0 = global_ns();
             ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
             ctl.evals = 1;
             ctl.unsafe = 0;
+            ctl.first_un = 0;
+            ctl.do_reset = 0;
             ctl.ph[0] = ctl.ph[1] = ctl.ph[2] = ctl.ph[3] = 0;
         }
         __syncthreads();
         const int qi = ctl.qi;
         if (qi < 0) break;  // work list exhausted
 
-        const int k = a.k_arr ? a.k_arr[qi] : a.k;
-        const int L = a.L_arr ? a.L_arr[qi] : a.L;
-        const int Mmax = a.M_arr ? a.M_arr[qi] : a.M;
-        const bool bad = k < 1 || k > a.k || L < k || L > a.L || Mmax < 1 || Mmax > a.M;
+        const bool bad = ctl.k < 1 || ctl.k > a.k || ctl.L < ctl.k || ctl.L > a.L || ctl.Mmax < 1 || ctl.Mmax > a.M;
         if (bad) {
             for (int i = tid; i < a.k; i += NT) {
                 a.out_ids[(size_t)qi * a.k + i] = -1;
@@ -120,22 +178,24 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             for (int i = tid; i < words; i += NT) table[i] = empty;
         }
         if (tid == 0) {
-            cand[0] = (entry_t)(uint32_t)a.entry;
-            ctl.ns = 0;
+            ctl.ns[0] = ctl.ns[1] = 0;
+            fresh[0] = (uint32_t)a.entry;
         }
         __syncthreads();
         // the entry point P: distance, queue = [P], visited = {P}
-        compute_keys_teams<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, 1, a.team_lanes, kEmptyEntry,
-                                      surv, &ctl.ns);
+        if (warp == 0)
+            warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, 1, a.team_lanes, kEmptyEntry, surv,
+                                             &ctl.ns[1]);
         __syncthreads();
         if (tid == 0) {
             Qa[0] = surv[0];
             visit_set(table, a, (uint32_t)a.entry);
             ctl.hash_count = 1;
+            ctl.ns[1] = 0;
         }
         __syncthreads();
 
-        int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
+        int Mcur = a.M0 < ctl.Mmax ? a.M0 : ctl.Mmax;
         int step = 0;
         int qlen = 1;  // the same in every thread
         entry_t *Q = Qa, *Qn = Qb;
@@ -148,205 +208,194 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         ctl.tmark = now_;                              \
     }
         for (;;) {
-            // --- forget the visited table when half full (keep the queued ids);
+            // --- forget the open-addressing table when half full (keep the queued ids);
             // the direct-mapped cache never resets, it forgets by eviction
-            if (a.visited_mode == 0 && ctl.hash_count * 2 > H) {
+            // (decided by thread 0 after the last step's distance barrier, so every thread sees one value)
+            if (ctl.do_reset) {
                 for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
                 __syncthreads();
                 for (int i = tid; i < qlen; i += NT) visited_insert(table, a.hash_bits, entry_id(Q[i]));
                 if (tid == 0) {
                     ctl.hash_count = qlen;
+                    ctl.do_reset = 0;
                     ctl.resets++;
                     ctl.unsafe = 1;
                 }
+                __syncthreads();
             }
-            // --- select the first Mcur unchecked entries (rank order) and mark them
-            if (warp == 0) {
-                int found = 0;
-                for (int b = 0; b < qlen && found < Mcur; b += 32) {
-                    const int i = b + lane;
-                    entry_t e = i < qlen ? Q[i] : kChecked;
-                    const bool un = !(e & kChecked);
-                    const unsigned bal = __ballot_sync(kFull, un);
-                    const int r = found + __popc(bal & ((1u << lane) - 1u));
-                    if (un && r < Mcur) {
-                        act[r] = (int)entry_id(e);
-                        Q[i] = e | kChecked;
-                    }
-                    found += __popc(bal);
+            const int par = step & 1;
+            // --- select: every warp computes the first Mcur unchecked entries (rank order) of the stable
+            // queue; rank r is this warp's if r mod NW == warp. Entries before first_un are all checked.
+            int found = 0, my_rows = 0, last_pos = -1;
+            for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
+                const int i = b + lane;
+                const entry_t e = i < qlen ? Q[i] : kChecked;
+                const bool un = !(e & kChecked);
+                const unsigned bal = __ballot_sync(kFull, un);
+                const int r = found + __popc(bal & lt_mask);
+                const bool take = un && r < Mcur;
+                if (take && (r % NW) == warp) {
+                    sel_id[r / NW] = (int)entry_id(e);
+                    sel_pos[r / NW] = i;
                 }
-                if (lane == 0) {
-                    ctl.nact = found < Mcur ? found : Mcur;
-                    ctl.ncand = 0;
-                    ctl.anydup = 0;
-                    ctl.ns = 0;
-                }
+                const unsigned tb = __ballot_sync(kFull, take);
+                if (tb) last_pos = b + 31 - __clz(tb);
+                found += __popc(bal);
             }
-            __syncthreads();
+            const int nact = found < Mcur ? found : Mcur;
+            if (nact == 0) break;  // no unchecked vertex left (identical in every warp)
+            my_rows = nact > warp ? (nact - warp + NW - 1) / NW : 0;
+            __syncwarp();
             ANN_PHASE(0)
-            const int nact = ctl.nact;
-            if (nact == 0) break;  // no unchecked vertex left
             step++;
-            if (tid == 0) {
-                ctl.steps++;
-                ctl.expansions += nact;
-            }
 
-            // --- expand: adjacency rows -> visited filter -> candidate ids
+            // --- expand this warp's rows: adjacency -> visited set -> fresh list (+ L2 prefetch)
+            int nf = 0;
             {
-                // Each thread issues all of its adjacency loads (up to four ids), then all of its visited
-                // updates, then the warp appends its fresh vertices with one scan and one atomic. The thread
-                // that finds a fresh vertex also asks L2 for its row.
-                constexpr int KA = 4;
-                const int total = nact * R;
-                for (int b0 = warp * 32; b0 < total; b0 += NT * KA) {
+                constexpr int KA = 4;  // row parts whose loads are in flight together
+                const int units = my_rows * SR;
+                for (int t0 = 0; t0 < units; t0 += KA) {
                     int u[KA];
 #pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        const int i = b0 + k * NT + lane;
-                        u[k] = -1;
-                        if (i < total) {
-                            const int aidx = i / R, r = i - aidx * R;
-                            u[k] = __ldg(a.adj + (size_t)act[aidx] * R + r);
+                    for (int kk = 0; kk < KA; ++kk) {
+                        const int t = t0 + kk;
+                        u[kk] = -1;
+                        if (t < units) {
+                            const int j = SR == 1 ? t : t / SR;
+                            const int slot = (t - j * SR) * 32 + lane;
+                            if (slot < R) u[kk] = __ldg(a.adj + (size_t)(uint32_t)sel_id[j] * (uint32_t)R + slot);
                         }
                     }
-                    unsigned fresh = 0;  // bit k: u[k] was not in the visited set
+                    unsigned fr = 0;  // bit kk: u[kk] was not in the visited set
                     bool forgot = false;
 #pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        if (u[k] >= 0) {
-                            const int ins = visit_set(table, a, (uint32_t)u[k]);
-                            if (ins != 0) fresh |= 1u << k;
+                    for (int kk = 0; kk < KA; ++kk) {
+                        if (u[kk] >= 0) {
+                            const int ins = visit_set(table, a, (uint32_t)u[kk]);
+                            if (ins != 0) fr |= 1u << kk;
                             if (ins >= 2) forgot = true;
                         }
                     }
                     if (forgot) ctl.unsafe = 1;  // a vertex may have been forgotten: repeats possible
-                    const int cnt = __popc(fresh);
+                    const int cnt = __popc(fr);
                     int incl = cnt;  // inclusive scan of the per-lane counts
 #pragma unroll
                     for (int off = 1; off < 32; off <<= 1) {
                         const int v = __shfl_up_sync(kFull, incl, off);
                         if (lane >= off) incl += v;
                     }
-                    int base = 0;
-                    if (lane == 31 && incl > 0) base = atomicAdd(&ctl.ncand, incl);
-                    int pos = __shfl_sync(kFull, base, 31) + incl - cnt;
+                    int pos = nf + incl - cnt;
 #pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        if (fresh >> k & 1u) {
-                            cand[pos++] = (entry_t)(uint32_t)u[k];
-                            if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u[k]);
+                    for (int kk = 0; kk < KA; ++kk) {
+                        if (fr >> kk & 1u) {
+                            fresh[pos++] = (uint32_t)u[kk];
+                            if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u[kk]);
                         }
                     }
+                    nf += __shfl_sync(kFull, incl, 31);
                 }
             }
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) {
+                if (nf) {
+                    atomicAdd(&ctl.wevals, nf);
+                    if (a.visited_mode == 0) atomicAdd(&ctl.hash_count, nf);
+                }
+            }
             ANN_PHASE(1)
-            const int nc = ctl.ncand;
+
+            // --- distances of this warp's fresh rows; only candidates below the L-th queued entry survive
+            const int L = ctl.L;
+            const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
+            // four chunks in flight per lane (one 128-d BF16 row per 4-lane team in one round trip)
+            warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, nf, a.team_lanes, limit, surv,
+                                             &ctl.ns[par]);
+            __syncthreads();
+            ANN_PHASE(2)
+            const int ns = ctl.ns[par];
+            if (lane < my_rows) Q[sel_pos[lane]] |= kChecked;  // the selection is taken: mark it
             if (tid == 0) {
-                ctl.hash_count += nc;
-                ctl.evals += nc;
+                ctl.ns[par ^ 1] = 0;  // next step's counter (last read before this step's barrier)
+                ctl.steps++;
+                ctl.expansions += nact;
+                ctl.first_un = last_pos + 1;
+                ctl.do_reset = a.visited_mode == 0 && ctl.hash_count * 2 > H;
             }
-            if (nc > 0) {
-                // --- distances; only candidates below the L-th queued entry survive
-                const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
-                if (STORE != ANN_STORE_E4M3 && a.tma_rows > 0) {
-                    if (!compute_keys_tma<STORE, NT>(a.base, a.d_pad, a.metric, qv, cand, nc, stage, a.tma_rows, bar,
-                                                     &parity, limit, surv, &ctl.ns)) {
-                        // a staging batch never arrived: fail this query, let the copies land, stop
-                        mbar_wait(bar, parity ^ 1u, 1 << 22);
-                        for (int i = tid; i < a.k; i += NT) {
-                            a.out_ids[(size_t)qi * a.k + i] = -1;
-                            a.out_dists[(size_t)qi * a.k + i] = __int_as_float(0x7f800000);
-                        }
-                        if (tid == 0 && a.stats) {
-                            ann_query_stats st = {};
-                            st.steps = -2;
-                            a.stats[qi] = st;
-                        }
-                        return;
+            if (ns > 0) {
+                // --- sort the survivors by (key, id) into srt
+                entry_t *srt = surv;
+                if (ns <= 32) {
+                    if (warp == 0) {
+                        entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
+                        e = warp_sort32(e);
+                        surv[lane] = e;
                     }
-                } else if (STORE != ANN_STORE_E4M3 && a.pipe_bytes > 0) {
-                    compute_keys_pipe<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, stage, limit, surv,
-                                                 &ctl.ns);
                     __syncthreads();
+                } else if (ns > 64 && ns <= NT) {
+                    // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
+                    block_rank_sort<NT>(surv, ns, cand);  // the fresh lists are not needed any more
+                    srt = cand;
                 } else {
-                    // four chunks in flight per lane: a few spilled registers outside the gather loop cost less
-                    // than a second round trip per row (measured 3-4 % faster than two)
-                    compute_keys_teams<STORE, NT, 4>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, a.team_lanes,
-                                                  limit, surv, &ctl.ns);
+                    int P = 64;
+                    while (P < ns) P <<= 1;
+                    for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
                     __syncthreads();
+                    block_bitonic_sort<NT>(surv, P);
                 }
-                ANN_PHASE(2)
-                const int ns = ctl.ns;
-                if (ns > 0) {
-                    // --- sort the survivors by (key, id) into srt
-                    entry_t *srt = surv;
-                    if (ns <= 32) {
+                int ncl = ns;
+                if (ctl.unsafe) {
+                    // --- drop ids already queued or repeated (only after the visited set forgot)
+                    int any = 0;
+                    for (int j = tid; j < ns; j += NT) {
+                        const entry_t c = srt[j];
+                        bool d = (j > 0 && srt[j - 1] == c);
+                        if (!d) {
+                            const int pos = count_below(Q, qlen, c);
+                            d = pos < qlen && (Q[pos] & kMask) == c;
+                        }
+                        dup[j] = d;
+                        any |= d;
+                    }
+                    if (__syncthreads_or(any)) {
                         if (warp == 0) {
-                            entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
-                            e = warp_sort32(e);
-                            surv[lane] = e;
+                            int outp = 0;
+                            for (int b = 0; b < ns; b += 32) {
+                                const int j = b + lane;
+                                const bool keep = j < ns && !dup[j];
+                                const entry_t c = j < ns ? srt[j] : 0ull;
+                                const unsigned bal = __ballot_sync(kFull, keep);
+                                if (keep) srt[outp + __popc(bal & lt_mask)] = c;
+                                outp += __popc(bal);
+                            }
+                            if (lane == 0) ctl.anydup = outp;
                         }
                         __syncthreads();
-                    } else if (ns > 64 && ns <= NT) {
-                        // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
-                        block_rank_sort<NT>(surv, ns, cand);  // the candidate ids are not needed any more
-                        srt = cand;
-                    } else {
-                        int P = 64;
-                        while (P < ns) P <<= 1;
-                        for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
-                        __syncthreads();
-                        block_bitonic_sort<NT>(surv, P);
+                        ncl = ctl.anydup;
+                        if (tid == 0) ctl.dropped += ns - ncl;
                     }
-                    int ncl = ns;
-                    if (ctl.unsafe) {
-                        // --- drop ids already queued or repeated (only after the table forgot)
-                        int any = 0;
-                        for (int j = tid; j < ns; j += NT) {
-                            const entry_t c = srt[j];
-                            bool d = (j > 0 && srt[j - 1] == c);
-                            if (!d) {
-                                const int pos = count_below(Q, qlen, c);
-                                d = pos < qlen && (Q[pos] & kMask) == c;
-                            }
-                            dup[j] = d;
-                            any |= d;
-                        }
-                        if (__syncthreads_or(any)) {
-                            if (warp == 0) {
-                                int outp = 0;
-                                for (int b = 0; b < ns; b += 32) {
-                                    const int j = b + lane;
-                                    const bool keep = j < ns && !dup[j];
-                                    const entry_t c = j < ns ? srt[j] : 0ull;
-                                    const unsigned bal = __ballot_sync(kFull, keep);
-                                    if (keep) srt[outp + __popc(bal & ((1u << lane) - 1u))] = c;
-                                    outp += __popc(bal);
-                                }
-                                if (lane == 0) ctl.anydup = outp;
-                            }
-                            __syncthreads();
-                            ncl = ctl.anydup;
-                            if (tid == 0) ctl.dropped += ns - ncl;
-                        }
-                    }
-                    // --- merge queue and survivors, truncated to L (merge path: one search per thread)
-                    block_merge_path<NT>(Q, qlen, srt, ncl, Qn, L);
-                    __syncthreads();  // the new queue is complete; nothing of the old one is read again
-                    qlen = min(L, qlen + ncl);
-                    entry_t *tmp = Q;
-                    Q = Qn;
-                    Qn = tmp;
                 }
+                // --- merge queue and survivors, truncated to L (merge path: one search per thread); the first
+                // survivor's rank among the old entries bounds the new queue's checked prefix
+                if (tid == 0 && ncl > 0) {
+                    const int p0 = count_below(Q, qlen, srt[0]);
+                    if (p0 < ctl.first_un) ctl.first_un = p0;
+                }
+                block_merge_path<NT>(Q, qlen, srt, ncl, Qn, ctl.L);
+                __syncthreads();  // the new queue is complete; nothing of the old one is read again
+                qlen = min(ctl.L, qlen + ncl);
+                entry_t *tmp = Q;
+                Q = Qn;
+                Qn = tmp;
+            } else {
+                __syncthreads();  // the marks and first_un are visible before the next select
             }
             ANN_PHASE(3)
-            if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
+            if (step % a.t == 0) Mcur = min(2 * Mcur, ctl.Mmax);
         }
 #undef ANN_PHASE
 
         // --- output: first k of the queue, optionally re-ranked with FP32 rows
+        const int k = ctl.k;
         const entry_t *res = Q;
         if (a.rerank) {
             for (int i = tid; i < qlen; i += NT) {
@@ -354,11 +403,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 cand[i] = (entry_t)id;
                 if (a.l2_prefetch) prefetch_row_l2(a.base32, (uint32_t)a.d_pad32 * 4u, id);
             }
-            if (tid == 0) ctl.ns = 0;
+            if (tid == 0) ctl.ns[0] = 0;
             __syncthreads();
             // every key is kept (limit = the empty entry), in whatever order the teams finish
-            compute_keys_teams<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen,
-                                                     a.team_lanes32, kEmptyEntry, surv, &ctl.ns);
+            compute_keys_teams_m<ANN_STORE_F32, NT, L2, 2>(a.base32, nullptr, a.d_pad32, qv, cand, qlen,
+                                                           a.team_lanes32, kEmptyEntry, surv, &ctl.ns[0]);
             __syncthreads();
             if (k <= 32) {
                 // only the k best are output: select them instead of sorting the whole queue
@@ -387,7 +436,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             ann_query_stats st;
             st.steps = ctl.steps;
             st.expansions = ctl.expansions;
-            st.evals = ctl.evals;
+            st.evals = ctl.evals + ctl.wevals;
             st.hash_resets = ctl.resets;
             st.dup_dropped = ctl.dropped;
             st.merges = 0;
@@ -402,9 +451,15 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     }
 }
 
+// One kernel per metric: the distance formula is a compile-time choice.
+template <int NT, int STORE>
+static auto sync_kernel_for(int metric) {
+    return metric == ANN_METRIC_L2 ? sync_search_kernel<NT, STORE, true> : sync_search_kernel<NT, STORE, false>;
+}
+
 template <int NT, int STORE>
 static cudaError_t launch_t(const SearchArgs &a, int smem, int grid, cudaStream_t s) {
-    auto fn = sync_search_kernel<NT, STORE>;
+    auto fn = sync_kernel_for<NT, STORE>(a.metric);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, NT, smem, s>>>(a);
@@ -412,8 +467,8 @@ static cudaError_t launch_t(const SearchArgs &a, int smem, int grid, cudaStream_
 }
 
 template <int NT, int STORE>
-static cudaError_t occ_t(int smem, int *bps) {
-    auto fn = sync_search_kernel<NT, STORE>;
+static cudaError_t occ_t(int metric, int smem, int *bps) {
+    auto fn = sync_kernel_for<NT, STORE>(metric);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, NT, smem);
@@ -433,8 +488,8 @@ static cudaError_t launch_nt(const SearchArgs &a, int storage, int smem, int gri
     ANN_DISPATCH_STORE(NT, launch_t, a, smem, grid, s)
 }
 template <int NT>
-static cudaError_t occ_nt(int storage, int smem, int *bps) {
-    ANN_DISPATCH_STORE(NT, occ_t, smem, bps)
+static cudaError_t occ_nt(int storage, int metric, int smem, int *bps) {
+    ANN_DISPATCH_STORE(NT, occ_t, metric, smem, bps)
 }
 
 cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, int smem, int grid,
@@ -448,12 +503,12 @@ cudaError_t launch_sync_search(const SearchArgs &a, int storage, int threads, in
     return cudaErrorInvalidValue;
 }
 
-cudaError_t sync_search_occupancy(int storage, int threads, int smem, int *bps) {
+cudaError_t sync_search_occupancy(int storage, int metric, int threads, int smem, int *bps) {
     switch (threads) {
-        case 64: return occ_nt<64>(storage, smem, bps);
-        case 128: return occ_nt<128>(storage, smem, bps);
-        case 256: return occ_nt<256>(storage, smem, bps);
-        case 512: return occ_nt<512>(storage, smem, bps);
+        case 64: return occ_nt<64>(storage, metric, smem, bps);
+        case 128: return occ_nt<128>(storage, metric, smem, bps);
+        case 256: return occ_nt<256>(storage, metric, smem, bps);
+        case 512: return occ_nt<512>(storage, metric, smem, bps);
     }
     return cudaErrorInvalidValue;
 }

@@ -64,14 +64,14 @@ class Index:
     @staticmethod
     def params(mode="sync", M0=1, t=1, R_ratio=0.8, rerank=False, threads=0, hash_bits=0,
                persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None,
-               order=None, cluster=0, phase_cycles=None, visited_mode=0, stage_bytes=0, lane_pipeline=0,
+               order=None, cluster=0, phase_cycles=None, visited_mode=0,
                l2_prefetch=0, team_lanes=0):
         return _abi.SearchParams(mode=_abi.MODE[mode], M0=M0, t=t, R_ratio=R_ratio, rerank=int(rerank),
                                  threads=threads, hash_bits=hash_bits, persistent=int(persistent),
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
                                  M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order),
                                  cluster=cluster, phase_cycles=_ptr(phase_cycles), visited_mode=visited_mode,
-                                 stage_bytes=stage_bytes, lane_pipeline=lane_pipeline, l2_prefetch=l2_prefetch,
+                                 l2_prefetch=l2_prefetch,
                                  team_lanes=team_lanes)
 
     def describe(self, nq, k, L, M, **kw):

@@ -147,8 +147,10 @@ def mixture_deep(n, nq, d=96, C=128, r=32, spread=1.0, noise=0.1, seed=400):
 
 # ------------------------------------------------------------ graph builder
 
-def _torch_device():
+def _torch_device(device=None):
     import torch
+    if device is not None:
+        return torch.device(device)
     return torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
 
 
@@ -296,11 +298,11 @@ def reachable_from(adj: np.ndarray, entry: int) -> np.ndarray:
     return mask
 
 
-def _nearest_among(x, targets, pool):
+def _nearest_among(x, targets, pool, device=None):
     """For each row index in ``targets``, the index in ``pool`` of the nearest
-    point by L2 (chunked GEMM on the torch device)."""
+    point by L2 (chunked GEMM on the torch device, or on ``device``)."""
     import torch
-    dev = _torch_device()
+    dev = _torch_device(device)
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
@@ -322,13 +324,15 @@ def _nearest_among(x, targets, pool):
 
 
 def repair_reachability(adj: np.ndarray, entry: int, knn: np.ndarray, x: np.ndarray,
-                        max_rounds: int = 256, per_round: int = 1024):
+                        max_rounds: int = 256, per_round: int = 1024, device=None):
     """Make every vertex reachable from ``entry``. Each round finds the
     unreachable set by BFS and links up to ``per_round`` of its vertices
     (evenly spaced by id) from their nearest reachable vertex that still has
     room (a free slot, else one of its last slots; at most R/2 slots of a row
     are given to such links); a link makes the whole part of the graph behind
-    that vertex reachable. Returns (adj, number of links added)."""
+    that vertex reachable. ``device`` forces the torch device of the
+    nearest-vertex search ("cpu" keeps the repair off the GPU). Returns (adj,
+    number of links added)."""
     adj = adj.copy()
     n, R = adj.shape
     protected = np.zeros((n, R), bool)
@@ -343,7 +347,7 @@ def repair_reachability(adj: np.ndarray, entry: int, knn: np.ndarray, x: np.ndar
         room = mask & (protected.sum(1) < max(1, R // 2))
         if not room.any():
             break
-        src = _nearest_among(x, pick, np.flatnonzero(room))
+        src = _nearest_among(x, pick, np.flatnonzero(room), device)
         for s_, u in zip(src.tolist(), pick.tolist()):
             row = adj[s_]
             if u in row or protected[s_].sum() >= max(1, R // 2):

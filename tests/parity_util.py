@@ -5,9 +5,9 @@ accepted when its FP64 key is within ``rel`` (1e-5) of the oracle's key at the
 same rank (a swap among near-equal distances); GPU keys (FP32) must be within
 ``rel`` of the FP64 key of the id they report. Queries on which the oracle
 logged a near-tie at a selection, truncation or output boundary may take a
-different trajectory under FP32 rounding; they are reported separately and
-judged by recall against the oracle's answer, and at least 90% of all rows
-must match. The near-tie window passed to the oracle is the FP32 error bound
+different trajectory under FP32 rounding. Such a row that fails the swap rule
+is "exempt": it is listed in the report, judged by recall against the
+oracle's answer, and at most 10% of the rows may be exempt. The near-tie window passed to the oracle is the FP32 error bound
 of the key (fp32_tie_window). For inner product the key tolerance is taken
 relative to |q| |x| rather than |key|, since the dot product cancels.
 
@@ -51,8 +51,13 @@ def fp32_tie_window(base, q, metric):
 
 
 def compare_float(gpu_ids, gpu_keys, orc_ids, orc_keys, tie_events, base, q, metric, rel=1e-5,
-                  min_tie_recall=0.9, min_match_frac=0.9):
-    """Returns a report dict; asserts the rules in the module docstring."""
+                  min_tie_recall=0.9, max_exempt_frac=0.1, label=""):
+    """Asserts the rules in the module docstring and returns a report dict.
+    A row is "exempt" when it fails the swap rule and the oracle logged a
+    near-tie on it; every exempt row is listed in the report (and printed),
+    at most ``max_exempt_frac`` of the rows may be exempt, and their mean
+    recall against the oracle must reach ``min_tie_recall``. A row that
+    fails the swap rule without a logged near-tie fails the comparison."""
     gpu_ids = np.asarray(gpu_ids)
     gpu_keys = np.asarray(gpu_keys, np.float64)
     k64 = fp64_keys(base, q, gpu_ids, metric)
@@ -71,16 +76,18 @@ def compare_float(gpu_ids, gpu_keys, orc_ids, orc_keys, tie_events, base, q, met
     assert bad_rows.size == 0, (
         f"{bad_rows.size} tie-free queries differ from the oracle, e.g. row {bad_rows[0]}: "
         f"gpu {gpu_ids[bad_rows[0]].tolist()} oracle {orc_ids[bad_rows[0]].tolist()}")
-    tie_rows = np.flatnonzero(~clean)
+    exempt = np.flatnonzero(~clean & ~good_rows)
     rec = 1.0
-    if tie_rows.size:
+    if exempt.size:
         rec = float(np.mean([len(set(gpu_ids[r].tolist()) & set(orc_ids[r].tolist())) / orc_ids.shape[1]
-                             for r in tie_rows]))
-        assert rec >= min_tie_recall, f"recall vs oracle on near-tie queries {rec}"
-    frac = float(good_rows.mean())
-    assert frac >= min_match_frac, f"only {frac:.3f} of the queries match the oracle"
-    return {"tie_free": int(clean.sum()), "tie_rows": int(tie_rows.size), "match_frac": frac,
-            "tie_recall": rec}
+                             for r in exempt]))
+    rep = {"rows": int(gpu_ids.shape[0]), "tie_free": int(clean.sum()), "tie_rows": int((~clean).sum()),
+           "tie_rows_within_swap_rule": int((~clean & good_rows).sum()), "exempt_rows": exempt.tolist(),
+           "exempt_recall": rec, "match_frac": float(good_rows.mean())}
+    print(f"compare_float{(' ' + label) if label else ''}: {rep}")
+    assert exempt.size <= max_exempt_frac * gpu_ids.shape[0], f"{exempt.size} exempt rows: {exempt.tolist()}"
+    assert rec >= min_tie_recall, f"recall vs oracle on the exempt rows {rec}"
+    return rep
 
 
 def compare_exact(gpu_ids, gpu_keys, orc_ids, orc_keys):
@@ -88,3 +95,31 @@ def compare_exact(gpu_ids, gpu_keys, orc_ids, orc_keys):
     g = np.asarray(gpu_keys, np.float64)
     o = np.asarray(orc_keys, np.float64)
     np.testing.assert_array_equal(g, o)
+
+
+def oracle_rows(oracle_mod, base, adj, entry, queries, ks, Ls, Ms, metric="l2", M0=1, t=1, nthreads=8):
+    """The oracle's top-M search of queries[i] with its own k, L, M (grouped
+    by (L, M): the search does not depend on k, which only cuts the output).
+    Returns per-row lists of ids and keys (length k) and steps, expansions,
+    evals arrays."""
+    n = len(ks)
+    ids = [None] * n
+    keys = [None] * n
+    steps = np.zeros(n, np.int64)
+    exps = np.zeros(n, np.int64)
+    evals = np.zeros(n, np.int64)
+    groups = {}
+    for i in range(n):
+        groups.setdefault((int(Ls[i]), int(Ms[i])), []).append(i)
+    for (L, M), rows in groups.items():
+        rows = np.asarray(rows)
+        K = int(max(ks[r] for r in rows))
+        o_ids, o_keys, o_st = oracle_mod.search(base, adj, entry, queries[rows], algo="topm", metric=metric,
+                                                L=L, K=K, M0=M0, M_max=M, t=t, nthreads=nthreads)
+        for j, r in enumerate(rows):
+            ids[r] = o_ids[j, :ks[r]]
+            keys[r] = o_keys[j, :ks[r]]
+            steps[r] = o_st["steps"][j]
+            exps[r] = o_st["expansions"][j]
+            evals[r] = o_st["evals"][j]
+    return ids, keys, steps, exps, evals

@@ -44,6 +44,38 @@ def test_batch_rows_equal_single_searches(setup):
     b.close()
 
 
+def test_batch_rows_equal_the_oracle(oracle_mod):
+    """A planned batch on integer-valued data (1..255 values, d = 128: every
+    FP32 sum is exact) with uneven k, L, M: every row's ids and keys equal
+    the oracle's top-M search of that query with its own k, L, M bit for
+    bit, and so do its steps and expansions (the forgetful visited cache can
+    only add distance evaluations)."""
+    from paper_2201_13007_gb300.index import Batch, Index, stats_dict
+    from parity_util import oracle_rows
+    w = synth.make_workload("sift", 20000, 600)
+    ix = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True)
+    g = np.random.default_rng(12)
+    nq = w.queries.shape[0]
+    k = g.choice([1, 10, 100], nq).astype(np.int32)
+    L = np.maximum(k, g.choice([32, 64, 128, 256, 512], nq)).astype(np.int32)
+    M = g.choice([1, 2, 4, 8, 16, 32], nq).astype(np.int32)
+    st = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
+    b = Batch(ix, k, L, M, stats=st, rerank=True)
+    ids, dists = b.search(torch.from_numpy(w.queries).cuda())
+    torch.cuda.synchronize()
+    ids, dists, s = ids.cpu().numpy(), dists.cpu().numpy(), stats_dict(st)
+    o_ids, o_keys, o_steps, o_exps, o_evals = oracle_rows(oracle_mod, w.base, w.adj, w.entry, w.queries, k, L, M)
+    for i in range(nq):
+        np.testing.assert_array_equal(ids[i, :k[i]], o_ids[i], err_msg=f"row {i}")
+        np.testing.assert_array_equal(dists[i, :k[i]].astype(np.float64), o_keys[i], err_msg=f"row {i}")
+        assert (ids[i, k[i]:] == -1).all()
+    np.testing.assert_array_equal(s["steps"], o_steps)
+    np.testing.assert_array_equal(s["expansions"], o_exps)
+    assert (s["evals"] >= o_evals).all()
+    b.close()
+    ix.close()
+
+
 def test_batch_under_cuda_graph_capture(setup):
     ix, Batch, w, k, L, M = setup
     q = torch.from_numpy(w.queries).cuda()

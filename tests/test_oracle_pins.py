@@ -97,6 +97,32 @@ def test_exact_knn_matches_scipy(oracle_mod, metric):
         np.testing.assert_allclose(keys[i], D[i][order], rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_exact_knn_gemm_equals_the_plain_sum_on_integer_data(oracle_mod, metric):
+    """The GEMM form of Def. 1 is exact when the coordinates are integers
+    (0..255 here, d = 128, with duplicated rows for exact ties): ids and keys
+    equal the plain per-coordinate sum's bit for bit, ties included."""
+    r = np.random.default_rng(6)
+    base = r.integers(0, 256, (3000, 128)).astype(np.float32)
+    base[100:140] = base[0:40]                       # exact key ties, broken by id
+    q = r.integers(0, 256, (37, 128)).astype(np.float32)
+    q[3] = base[5]
+    ids, keys = oracle_mod.exact_knn(base, q, 15, metric=metric, nthreads=4)
+    gi, gk = oracle_mod.exact_knn_gemm(base, q, 15, metric=metric, chunk=8)
+    np.testing.assert_array_equal(gi, ids)
+    np.testing.assert_array_equal(gk, keys)
+
+
+def test_exact_knn_gemm_float_data_within_fp64_rounding(oracle_mod):
+    r = np.random.default_rng(7)
+    base = r.standard_normal((2000, 24)).astype(np.float32)
+    q = r.standard_normal((20, 24)).astype(np.float32)
+    ids, keys = oracle_mod.exact_knn(base, q, 10)
+    gi, gk = oracle_mod.exact_knn_gemm(base, q, 10)
+    np.testing.assert_array_equal(gi, ids)  # no near-ties at this size
+    np.testing.assert_allclose(gk, keys, rtol=1e-12, atol=1e-12)
+
+
 def test_exact_knn_pads_when_k_exceeds_n(oracle_mod):
     base = np.arange(3, dtype=np.float32).reshape(3, 1)
     ids, keys = oracle_mod.exact_knn(base, np.array([[0.2]], np.float32), 5)

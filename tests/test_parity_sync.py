@@ -50,14 +50,16 @@ def test_tiny_float_parity(ann, oracle_mod, tiny, L, M):
     o_ids, o_keys, o_st = oracle_mod.search(tiny.base, tiny.adj, tiny.entry, tiny.queries, algo="topm",
                                             L=L, K=10, M0=1, M_max=M, t=1, nthreads=8,
                                             tie_tol=fp32_tie_window(tiny.base, tiny.queries, "l2")[0])
-    rep = compare_float(ids, dists, o_ids, o_keys, o_st["tie_events"], tiny.base, tiny.queries, "l2")
+    rep = compare_float(ids, dists, o_ids, o_keys, o_st["tie_events"], tiny.base, tiny.queries, "l2",
+                        label=f"tiny L={L} M={M}")
     s = stats_dict(st)
     clean = (o_st["tie_events"] == 0)
     assert (s["hash_resets"] == 0).all()
     # with no forgotten vertices the distance count is exactly |V| of the oracle
     np.testing.assert_array_equal(s["evals"][clean], o_st["evals"][clean])
     np.testing.assert_array_equal(s["steps"][clean], o_st["steps"][clean])
-    assert rep["tie_free"] >= 30
+    # every row either matches the oracle (up to swaps of near-equal keys) or is listed as exempt
+    assert rep["match_frac"] >= 0.95, rep
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
@@ -235,6 +237,35 @@ def test_reduced_precision_with_rerank(ann, oracle_mod, storage):
     ix.close()
 
 
+@pytest.mark.parametrize("storage", ["e4m3", "f16"])
+def test_high_dimension_d960_with_rerank(ann, oracle_mod, storage):
+    """The high-dimension workload's shape (d = 960, log-normal mixture) in
+    FP8-E4M3 with per-vector scales and in FP16, with the launch the library
+    chooses: the search follows the oracle run on the stored values within
+    the FP32 error bound, and the FP32 re-rank equals the oracle's re-rank
+    of its final queue."""
+    _, Index, _ = ann
+    w = synth.make_workload("gist", 20000, 64)
+    assert w.d == 960
+    L, M = 128, 8
+    stored = oracle_mod.stored_values(w.base, storage)
+    ix = Index(w.base, w.adj, w.entry, storage=storage, keep_f32=True)
+    q = torch.from_numpy(w.queries).cuda()
+    ids_nr, d_nr = ix.search(q, L, L, M)              # the whole final queue, stored keys
+    ids_rr, d_rr = ix.search(q, 10, L, M, rerank=True)
+    torch.cuda.synchronize()
+    o_ids, o_keys, o_st = oracle_mod.search(stored, w.adj, w.entry, w.queries, algo="topm", L=L, K=L,
+                                            M0=1, M_max=M, t=1, nthreads=8,
+                                            tie_tol=fp32_tie_window(stored, w.queries, "l2")[0])
+    compare_float(ids_nr.cpu().numpy(), d_nr.cpu().numpy(), o_ids, o_keys, o_st["tie_events"], stored,
+                  w.queries, "l2", label=f"d=960 {storage} stored keys")
+    clean = o_st["tie_events"] == 0
+    r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, o_ids, 10)
+    compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
+                  np.zeros(clean.sum()), w.base, w.queries[clean], "l2", label=f"d=960 {storage} re-rank")
+    ix.close()
+
+
 @pytest.mark.parametrize("visited_mode,slot_bytes", [(2, 1), (3, 4)])
 @pytest.mark.parametrize("hash_bits", [8, 10, 12])
 def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash_bits, visited_mode, slot_bytes):
@@ -253,39 +284,6 @@ def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash
     compare_exact(ids, dists, o_ids, o_keys)
     s = stats_dict(st)
     assert (s["evals"] >= o_st["evals"]).all()
-
-
-@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("stage_bytes", [1, 8192, 65536])
-def test_bulk_copy_staging_exact(ann, oracle_mod, sift_small, storage, stage_bytes):
-    """Rows staged by cp.async.bulk into shared memory (one row per copy,
-    completing on an mbarrier) give exactly the register-gather answers;
-    integer data, so also exactly the oracle's (FP16 holds 0..255 exactly)."""
-    _, Index, stats_dict = ann
-    w = sift_small
-    for L, M in ((64, 4), (200, 16)):
-        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, stage_bytes=stage_bytes,
-                              visited_mode=1)
-        o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
-                                                M0=1, M_max=M, t=1, nthreads=8)
-        compare_exact(ids, dists, o_ids, o_keys)
-        np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
-
-
-@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("threads", [128, 512])
-def test_lane_pipeline_exact(ann, oracle_mod, sift_small, storage, threads):
-    """Rows streamed through each lane's cp.async ring give exactly the
-    oracle's answers (integer data)."""
-    _, Index, stats_dict = ann
-    w = sift_small
-    for L, M in ((16, 1), (64, 4), (200, 16), (128, 32)):
-        ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, lane_pipeline=1, threads=threads,
-                              visited_mode=1)
-        o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
-                                                M0=1, M_max=M, t=1, nthreads=8)
-        compare_exact(ids, dists, o_ids, o_keys)
-        np.testing.assert_array_equal(stats_dict(st)["evals"], o_st["evals"])
 
 
 _TEAM_ORACLE = {}

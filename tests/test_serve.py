@@ -72,6 +72,15 @@ def test_each_result_equals_its_standalone_search(setup):
     finally:
         _abi.ann_serve_destroy(srv)
     assert len(out) == n
+    # each answer equals the oracle's search of that query with its own k, L, M: integer-valued data, so
+    # ids and keys are bit-exact
+    from parity_util import oracle_rows
+    import oracle
+    oracle.build()
+    o_ids, o_keys = oracle_rows(oracle, w.base, w.adj, w.entry, w.queries[qi], ks, Ls, Ms)[:2]
+    for t in range(n):
+        np.testing.assert_array_equal(out[t][2], o_ids[t], err_msg=f"request {t}")
+        np.testing.assert_array_equal(out[t][3].astype(np.float64), o_keys[t], err_msg=f"request {t}")
     # each answer equals the same query searched alone with its own k, L, M
     qd = torch.from_numpy(w.queries).cuda()
     for t in range(n):

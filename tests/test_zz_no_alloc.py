@@ -1,11 +1,13 @@
 """The allocation-free host-buffer search (ann_search_host_noalloc).
 
-Some callers cannot allocate device memory when they search (a thread that
-is capturing a CUDA graph, a process whose device memory is held by another
-framework's allocator); this entry point keeps its device scratch in one
-static device array instead. Here it must give the same answers as the
-ordinary host-buffer search (ann_search_host) on two calls in a row with
-different batches, and refuse a batch that does not fit its scratch.
+Some callers cannot allocate device memory when they search (a process
+whose device memory is reserved up front by another framework's caching
+allocator, a latency-critical thread that must not enter the CUDA
+allocator); this entry point keeps its device scratch in one static device
+array instead. Here it must give the same answers as the ordinary
+host-buffer search (ann_search_host) on two calls in a row with different
+batches, refuse a batch that does not fit its scratch, and refuse a cluster
+launch it does not make.
 
 This file is named to be collected last so that a run that stops at the
 first failure has already run every other test; it builds its own inputs and
@@ -32,7 +34,7 @@ def index():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     torch.cuda.init()
-    w = synth.make_workload("sift", 20000, 64)
+    w = synth.make_workload("sift", 20000, 2000)
     base = np.ascontiguousarray(w.base, np.float32)
     adj = np.ascontiguousarray(w.adj, np.int32)
     h = _abi.ann_index_create(_vp(base), w.n, w.d, _abi.STORAGE["bf16"], _vp(adj), w.R, w.entry,
@@ -61,6 +63,44 @@ def test_matches_host_search_on_two_calls(index, mode, rerank):
         np.testing.assert_array_equal(b_ids, a_ids)
         np.testing.assert_array_equal(b_d, a_d)
         assert (b_ids >= 0).all()
+
+
+def _recall(ids, gt):
+    return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / gt.shape[1] for a, b in zip(ids, gt)]))
+
+
+def test_async_walkers_on_two_calls(index, oracle_mod):
+    """The asynchronous walkers (one warp per walker, persistent grid) draw
+    their queries from the static array's counter and stage queries and
+    results there too. Their interleaving is not deterministic, so each call
+    is judged like the other asynchronous tests: every answer valid (distinct
+    ids, exact keys on this integer data, (key, id) order) and recall@10
+    against the exact top-10 within 0.003 of ann_search_host on the same
+    batch (2,000 queries x 10: one id is 5e-5 of recall)."""
+    h, w = index
+    params = _abi.SearchParams(mode=_abi.MODE["async"], R_ratio=0.8)
+    gt = oracle_mod.exact_knn(w.base, w.queries, 10, nthreads=8)[0]
+    for sl in (slice(0, 2000), slice(1000, 2000)):
+        q = np.ascontiguousarray(w.queries[sl])
+        a_ids, _ = _run(_abi.ann_search_host, h, q, 10, 64, 4, params)
+        b_ids, b_d = _run(_abi.ann_search_host_noalloc, h, q, 10, 64, 4, params)
+        assert (b_ids >= 0).all()
+        for i in range(q.shape[0]):
+            r = b_ids[i]
+            assert len(set(r.tolist())) == r.size
+            k64 = ((w.base[r].astype(np.float64) - q[i].astype(np.float64)) ** 2).sum(1)
+            np.testing.assert_array_equal(b_d[i].astype(np.float64), k64)
+            assert (np.lexsort((r, k64)) == np.arange(r.size)).all()
+        ra, rb = _recall(a_ids, gt[sl]), _recall(b_ids, gt[sl])
+        assert abs(ra - rb) <= 0.003, (ra, rb)
+
+
+def test_rejects_cluster_launch(index):
+    h, w = index
+    q = np.ascontiguousarray(w.queries[:8])
+    with pytest.raises(_abi.AnnError) as ei:
+        _run(_abi.ann_search_host_noalloc, h, q, 10, 64, 4, _abi.SearchParams(cluster=4))
+    assert ei.value.code == _abi.ANN_ERR_ARG and "one CTA per query" in str(ei.value)
 
 
 def test_rejects_batch_beyond_static_scratch(index):
