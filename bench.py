@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 
 K = 10
 TARGETS = (0.9, 0.99)
+CALIB = 2000  # queries the operating points are chosen on; recall is also reported on the others
 L_SWEEP = (10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024,
            1280, 1536, 2048)
 M_SWEEP = (4, 8, 16, 32)
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--workload", default="sift", choices=["sift", "gist", "deep-batch", "serve"],
                     help="sift: the headline (default); the others measure the precision, batching and serving "
                          "workloads and print one JSON line each")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the neighbour-grouping, precision and batching legs of the default run")
     ap.add_argument("--kernel-digest", action="store_true",
                     help="print the digest of the CUDA sources that an ncu summary records, and exit")
     return ap.parse_args()
@@ -247,20 +250,23 @@ def run_ours(args):
     forms = {k: v for k, v in forms.items() if k in wanted}
     head_name = next(iter(forms))
 
-    # ---- operating points: cheapest (L, M) reaching each recall target
+    # ---- operating points: cheapest (L, M) reaching each recall target on the calibration queries (the
+    # first CALIB of the batch); recall is then reported on the held-out rest as well as on the whole batch
     sweep = {}
+    calib = min(CALIB, max(1, nq // 5))
+    qc = q[:calib]
     for name, (ix, kw, _) in forms.items():
         if args.point:
             break
         for M in M_SWEEP:
             for L in L_SWEEP:
-                ids, _ = ix.search(q, K, L, M, **kw)
+                ids, _ = ix.search(qc, K, L, M, **kw)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                ids, _ = ix.search(q, K, L, M, **kw)
+                ids, _ = ix.search(qc, K, L, M, **kw)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
-                rec = recall_at_k(ids.cpu().numpy(), gt)
+                rec = recall_at_k(ids.cpu().numpy(), gt[:calib])
                 sweep[(name, L, M)] = (rec, dt)
                 if rec >= max(TARGETS) + 0.003:
                     break
@@ -324,7 +330,8 @@ def run_ours(args):
             bx = algorithmic_bytes(sx, w.R, row_bytes, w.d, K, L if kw.get("rerank") else 0)
             results[(name, tgt)] = {
                 "launch": ix.describe(nq, K, L, M, **kw),
-                "L": L, "M": M, "recall": recall_at_k(ids, gt), "ms_per_step": t * 1e3,
+                "L": L, "M": M, "recall": recall_at_k(ids, gt), "recall_held_out": recall_at_k(ids[calib:], gt[calib:]),
+                "ms_per_step": t * 1e3,
                 "qps": nq * world / t, "p50_us": float(np.percentile(svc, 50)),
                 "p99_us": float(np.percentile(svc, 99)), "alg_bytes": b, "gbs": b / t / 1e9,
                 "evals_per_query": float(st[:, 2].mean()), "steps_per_query": float(st[:, 0].mean()),
@@ -350,13 +357,24 @@ def run_ours(args):
                                    "qps": nq * world / t, "evals_per_query": float(sn[:, 2].mean()),
                                    "merges_per_query": float(sn[:, 5].mean())}
 
+    # ---- neighbour grouping (Sec. 4.4, degree-centric): the headline launch on the same index with the
+    # hottest 1 % of vertices by in-degree grouped, the block of a hot vertex prefetched whole or only its
+    # fresh rows; answers must not change
+    grouping = {}
+    if ix16 is not None and not args.no_legs:
+        try:
+            grouping = grouping_leg(torch, w, ix16, forms[head[0]][1], points[head], q, flush, args)
+        except Exception as e:  # the headline stands without this leg
+            grouping = {"error": repr(e)}
+            log("grouping leg failed:", e)
+
     # ---- plain one query per launch (latency form) on a subset
     single = {}
     for tgt in TARGETS:
         if args.skip_single or ("plain_f32", tgt) not in points:
             continue
         L, M = points[("plain_f32", tgt)]
-        for C in (1, 4, 8):  # one CTA, or a cluster of C CTAs per query
+        for C in (1, 2, 4, 8):  # one CTA, or a cluster of C CTAs per query
             lat = []
             for i in range(300):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -424,7 +442,10 @@ def run_ours(args):
                    "global_batch": nq * world, "L": h["L"], "M": h["M"],
                    "parallelism": f"replicas x{world} (queries sharded, no collective)",
                    "l2": "flushed (512 MB write) between timed steps; base 256 MB BF16 + 512 MB FP32 > L2"},
-        "recall@10": h["recall"], "p50_us": h["p50_us"], "p99_us": h["p99_us"],
+        "recall@10": h["recall"], "recall@10_held_out": h["recall_held_out"],
+        "operating_point": f"chosen on the first {calib} queries; recall@10_held_out is over the other "
+                           f"{nq - calib}",
+        "p50_us": h["p50_us"], "p99_us": h["p99_us"],
         "latency_kind": "per-query device service time (globaltimer, start to results written)",
         "roofline": {"bound": "hbm", "achieved": h["gbs_exact_visited"], "peak": hbm, "unit": "GB/s",
                      "frac": h["gbs_exact_visited"] / hbm, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
@@ -448,8 +469,20 @@ def run_ours(args):
         "points": {f"{nm}@{tgt}": v for (nm, tgt), v in results.items()},
         "one_query_per_launch": {str(k): v for k, v in single.items()},
         "async_alg3_bf16_rerank": async_pts,
+        "neighbour_grouping": grouping,
         "setup_s": setup_s,
     }
+    # the precision (1M x 960) and batching (100,000 uneven queries) workloads, short, as extra keys
+    if not args.no_legs and world == 1:
+        for name, fn in (("gist_precision", gist_leg), ("deep_batch", deep_batch_leg)):
+            try:
+                t0 = time.time()
+                out[name] = fn(torch, args)
+                out[name]["wall_s"] = time.time() - t0
+            except Exception as e:
+                out[name] = {"error": repr(e)}
+                log(f"{name} leg failed:", e)
+            torch.cuda.empty_cache()
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -587,6 +620,138 @@ def cheapest_points(torch, search, q, gt, Ls, Ms, targets, k=K):
         dt, L, M, rec = min(ok)
         pts[tgt] = (L, M, rec)
     return pts
+
+
+# ------------------------------------------------------ default-run legs
+
+def hot_vertices(adj, frac):
+    """The round(frac * n) vertices with the most in-edges, ties to the smaller
+    id (the library's rule for neighbour groups)."""
+    n = adj.shape[0]
+    deg = np.bincount(adj[adj >= 0].ravel(), minlength=n)
+    H = int(round(frac * n))
+    order = np.lexsort((np.arange(n), -deg))
+    return order[:H]
+
+
+def grouping_leg(torch, w, ix, kw, point, q, flush, args):
+    import oracle
+    L, M = point
+    nq = q.shape[0]
+    ids0, d0 = ix.search(q, K, L, M, **kw)
+    t_plain = float(np.mean(event_time(torch, lambda: ix.search(q, K, L, M, **kw), args.steps, args.warmup, flush)))
+    out = {"L": L, "M": M, "plain": {"ms": t_plain * 1e3, "qps": nq / t_plain}}
+    frac = 0.01
+    for pf in ("block", "rows"):
+        ix.group_neighbors(frac, pf)
+        ids, d = ix.search(q, K, L, M, **kw)
+        t = float(np.mean(event_time(torch, lambda: ix.search(q, K, L, M, **kw), args.steps, args.warmup, flush)))
+        out[f"hot{frac}_{pf}"] = {"ms": t * 1e3, "qps": nq / t, "speedup": t_plain / t,
+                                  "same_answers": bool(torch.equal(ids, ids0) and torch.equal(d, d0))}
+    ix.group_neighbors(0.0)
+    # how many expansions land on a grouped vertex (the oracle's expansion order on a sample of queries)
+    hot = np.zeros(w.n, bool)
+    hot[hot_vertices(w.adj, frac)] = True
+    oracle.build()
+    ex = hit = 0
+    for i in range(0, nq, nq // 24):
+        tr = oracle.search_trace(w.base, w.adj, w.entry, w.queries[i], algo="topm", L=L, K=K, M0=1, M_max=M, t=1)
+        ex += tr["expanded"].size
+        hit += int(hot[tr["expanded"]].sum())
+    out["hot_fraction_of_expansions"] = hit / max(ex, 1)
+    out["hot_vertices"] = int(hot.sum())
+    out["extra_hbm_bytes"] = int(hot.sum()) * w.R * ix.info()["d_pad"] * 2
+    return out
+
+
+# fixed operating points of the precision and batching legs: the cheapest (L, M) of the full sweeps
+# (`--workload gist | deep-batch`) that reach each recall target; recall at a given (L, M) is a property of
+# the method and the graph, not of the kernels, so these points hold while the kernels change
+GIST_POINTS = {"f32": {0.9: (128, 8), 0.99: (768, 8)}, "f16_rerank": {0.9: (128, 16), 0.99: (768, 16)},
+               "e4m3_rerank": {0.9: (128, 8), 0.99: (768, 16)}}
+
+
+def gist_leg(torch, args):
+    from paper_2201_13007_gb300 import synth
+    from paper_2201_13007_gb300.index import Index
+    w = synth.make_workload("gist", 1_000_000, 1000)
+    gt = exact_topk_gpu(w.base, w.queries, K, torch)
+    torch.cuda.empty_cache()
+    q = torch.from_numpy(w.queries).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    hbm, _ = peaks()
+    out = {"workload": "gist-like 1M x 960 (log-normal 32-component mixture), degree-32 graph, 1,000 queries, "
+                       "k=10, L2; fixed operating points", "points": {}}
+    for name, (stor, rr, es) in {"f16_rerank": ("f16", True, 2), "e4m3_rerank": ("e4m3", True, 1),
+                                 "f32": ("f32", False, 4)}.items():
+        ix = Index(w.base, w.adj, w.entry, storage=stor, keep_f32=rr)
+        for tgt, (L, M) in GIST_POINTS[name].items():
+            st = torch.empty((q.shape[0], 8), dtype=torch.int64, device="cuda")
+            ids, dd = ix.search(q, K, L, M, rerank=rr, persistent=True, stats=st)
+            t = float(np.mean(event_time(torch, lambda: ix.search(q, K, L, M, rerank=rr, persistent=True),
+                                         max(3, args.steps // 4), 2, flush)))
+            sn = st.cpu().numpy()
+            row = ix.info()["d_pad"] * es + (4 if stor == "e4m3" else 0)
+            b = algorithmic_bytes(sn, w.R, row, w.d, K, L if rr else 0)
+            out["points"][f"{name}@{tgt}"] = {"L": L, "M": M, "recall@10": recall_at_k(ids.cpu().numpy(), gt),
+                                              "qps": q.shape[0] / t, "ms_per_step": t * 1e3, "gbs": b / t / 1e9,
+                                              "frac": b / t / 1e9 / hbm, "evals_per_query": float(sn[:, 2].mean())}
+        ix.close()
+    return out
+
+
+def deep_batch_leg(torch, args):
+    from paper_2201_13007_gb300 import autotune, synth
+    from paper_2201_13007_gb300.index import Batch, Index
+    nq = 100_000
+    w = synth.make_workload("deep", 1_000_000, nq)
+    g = np.random.Generator(np.random.PCG64(4))
+    k = g.choice([1, 10, 100], nq).astype(np.int32)
+    Lc = np.array([32, 64, 128, 256, 512, 1024])
+    L = g.choice(Lc, nq)
+    while (L < k).any():
+        bad = L < k
+        L[bad] = g.choice(Lc, int(bad.sum()))
+    L = L.astype(np.int32)
+    M = g.choice([1, 2, 4, 8, 16, 32], nq).astype(np.int32)
+    ix = Index(w.base, w.adj, w.entry, metric="ip")
+    q = torch.from_numpy(w.queries).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    cfg = autotune.tune_buckets(ix, q, k, L, M, sample=2000, reps=1)
+    tune_s = time.time() - t0
+    b = Batch(ix, k, L, M, buckets=cfg)
+    ids, dists = b.search(q)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.search(q, out=(ids, dists), stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.search(q, out=(ids, dists))
+    t_graph = float(np.mean(event_time(torch, graph.replay, max(3, args.steps // 4), 2, flush)))
+    sample = np.arange(0, nq, 100)
+    gt = exact_topk_gpu(w.base, w.queries[sample], 100, torch, metric="ip")
+    idn = ids.cpu().numpy()
+    rec = np.mean([len(set(idn[i, :k[i]].tolist()) & set(gt[j, :k[i]].tolist())) / k[i]
+                   for j, i in enumerate(sample)])
+    lat = []
+    for i in np.arange(0, nq, 500):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.search(q[i:i + 1], int(k[i]), int(L[i]), int(M[i]))
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1) * 1e3)
+    ix.close()
+    return {"workload": "deep-like 1M x 96 unit vectors (inner product), 100,000 queries, k in {1,10,100}, "
+                        "L in {32..1024}, M in {1..32}", "buckets": cfg, "tune_s": tune_s,
+            "graph_replay_qps": nq / t_graph, "ms_per_step": t_graph * 1e3,
+            "mean_recall@k_sample": float(rec), "recall_sample": int(sample.size),
+            "one_launch_per_query": {"qps": 1e6 / float(np.mean(lat)), "p50_us": float(np.percentile(lat, 50)),
+                                     "p99_us": float(np.percentile(lat, 99)), "sample": len(lat)}}
 
 
 # --------------------------------------------- precision at high dimension

@@ -77,6 +77,7 @@ typedef struct {
     int32_t has_f32;     /* 1 if an FP32 copy is kept for re-rank */
     int64_t entry;
     int64_t device_bytes; /* HBM held by the index */
+    int64_t n_hot;        /* vertices with a neighbour group (ann_index_group_neighbors) */
 } ann_index_info;
 
 /* Per-query counters, written by the search kernels when requested. */
@@ -138,11 +139,17 @@ typedef struct {
      * slot only the bits of the (bijectively) hashed id that the slot index
      * does not already fix: one byte per slot while the ids need at most
      * hash_bits + 7 bits, two bytes up to hash_bits + 15, else a full id;
-     * 3 = the same cache with a full 32-bit id per slot. 2 and 3 are for the
-     * one-CTA sync kernel only. 0 = auto (for the one-CTA sync kernel 2 when
-     * L >= 128, else 3; otherwise 1). No form ever reports a vertex it did
-     * not see; they only forget, which changes the number of distance
-     * evaluations but never the results. */
+     * 3 = the same cache with a full 32-bit id per slot; 4 = a
+     * set-associative cache: 2^hash_bits sets of one 32-bit word, each
+     * holding the tags (the same split of the hashed id) of the 3 (or, for
+     * ids too long for three, 2) vertices that entered the set last; a
+     * fourth evicts the oldest. 2 and 3 are for the one-CTA sync kernel
+     * only, 4 for the one-CTA sync and async kernels. 0 = auto (one-CTA sync
+     * kernel: 4 when L >= 128, else 3; async walkers: 4; clusters: 1). No
+     * form ever reports a vertex it did not see; they only forget. In sync
+     * mode that changes the number of distance evaluations but never the
+     * results; asynchronous walkers may also queue and expand a forgotten
+     * vertex again, which changes when Algorithm 2 merges. */
     int32_t visited_mode;
     /* Sync kernels: 1 = the row of every vertex that passes the visited
      * filter is requested into L2 with one bulk prefetch
@@ -184,6 +191,22 @@ void ann_index_destroy(ann_index *index);
 /* Shape and storage of an index. */
 int ann_index_get_info(const ann_index *index, ann_index_info *info);
 
+/* Neighbour grouping (Sec. 4.4, cache-friendly neighbour grouping, in its
+ * degree-centric form): for the round(hot_fraction * n) vertices with the
+ * most in-edges (ties: the smaller id), store a copy of their R neighbours'
+ * stored rows contiguously, in adjacency order, after the n base rows (and
+ * scales). When the one-CTA sync kernel expands such a vertex it reads the
+ * fresh neighbours' vectors from that block instead of from R scattered
+ * rows; prefetch = 0 asks L2 for the whole block with one bulk prefetch when
+ * the vertex is expanded, prefetch = 1 asks only for the fresh rows, as for
+ * other vertices. The copies hold the same values, so results do not
+ * change. Vertex ids are not relabelled (they fix the (key, id) order of
+ * every result). hot_fraction in [0, 0.05]; 0 removes the grouping. Costs
+ * hot_fraction * n * R extra rows of HBM. Synchronous; no search may be in
+ * flight on the index. Errors: ANN_ERR_ARG, ANN_ERR_STATE (wrong device),
+ * ANN_ERR_OOM, ANN_ERR_CUDA. */
+int ann_index_group_neighbors(ann_index *index, float hot_fraction, int32_t prefetch);
+
 /* Search nq queries (Algorithm 1 / Sec. 4.1-4.2 top-M with M doubling from 1,
  * one CTA per query).
  *   queries    device, nq x d float32 row-major.
@@ -213,7 +236,8 @@ typedef struct {
     int32_t hash_bits;    /* log2 slots of the visited table */
     int32_t cluster;      /* CTAs per query */
     int32_t mode;         /* ann_mode */
-    int32_t visited_slot_bytes; /* bytes per visited-set slot: 1 or 2 (tags), 4 (ids) */
+    int32_t visited_slot_bytes; /* bytes per visited-set slot: 1 or 2 (tags), 4 (ids or a set word) */
+    int32_t visited_ways;       /* set-associative visited cache: tags per set word (2 or 3); 0 = other form */
 } ann_launch_info;
 
 int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L, int32_t M,

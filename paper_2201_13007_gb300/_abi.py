@@ -32,7 +32,7 @@ class IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("d_pad", ctypes.c_int32),
                 ("R", ctypes.c_int32), ("storage", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("has_f32", ctypes.c_int32), ("entry", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_hot", ctypes.c_int64)]
 
 
 class QueryStats(ctypes.Structure):
@@ -74,7 +74,7 @@ class Result(ctypes.Structure):
 class LaunchInfo(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("hash_bits", ctypes.c_int32), ("cluster", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("visited_slot_bytes", ctypes.c_int32)]
+                ("visited_slot_bytes", ctypes.c_int32), ("visited_ways", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -97,6 +97,7 @@ def lib():
             L.ann_index_destroy.argtypes = [vp]
             L.ann_index_destroy.restype = None
             L.ann_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+            L.ann_index_group_neighbors.argtypes = [vp, ctypes.c_float, i32]
             L.ann_search.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
             L.ann_search_ex.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
@@ -144,6 +145,10 @@ def ann_index_get_info(index) -> IndexInfo:
     info = IndexInfo()
     _check(lib().ann_index_get_info(index, ctypes.byref(info)))
     return info
+
+
+def ann_index_group_neighbors(index, hot_fraction, prefetch) -> None:
+    _check(lib().ann_index_group_neighbors(index, float(hot_fraction), int(prefetch)))
 
 
 def ann_search(index, queries, nq, k, L, M, out_ids, out_dists, stream) -> None:

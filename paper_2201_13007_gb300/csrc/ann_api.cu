@@ -8,6 +8,8 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <vector>
+#include <algorithm>
 
 #include "ann_internal.cuh"
 
@@ -53,6 +55,7 @@ void free_index_data(ann::IndexData &x) {
     cudaFree(x.adj);
     cudaFree(x.stage);
     cudaFree(x.work_counter);
+    cudaFree(x.hot_slot);
     x = ann::IndexData();
 }
 
@@ -218,16 +221,33 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
             return fail(ANN_ERR_ARG, "threads=%d not in {64,128,256,512}", threads);
         if (csize > 1 && threads == 64) threads = 128;
     }
-    // visited set: 1 = open addressing; 2 = direct-mapped cache of tags; 3 = direct-mapped cache of ids
-    if (p->visited_mode < 0 || p->visited_mode > 3)
-        return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2, 3}", p->visited_mode);
-    if (p->visited_mode >= 2 && (async || csize > 1))
-        return fail(ANN_ERR_ARG, "the direct-mapped visited cache is for the one-CTA sync kernel");
-    // auto: tags for queues of 128 or more (thousands of vertices visited: capacity pays), full ids below
-    // (a 2^12-id cache already holds what a short search visits, and its exchange is cheaper than a CAS)
-    const int vmode = p->visited_mode == 0 ? ((async || csize > 1) ? 1 : (L >= 128 ? 2 : 3)) : p->visited_mode;
+    // visited set: 1 = open addressing; 2 = direct-mapped cache of tags; 3 = direct-mapped cache of ids;
+    // 4 = set-associative cache of tags (2 or 3 ways per 32-bit set word)
+    if (p->visited_mode < 0 || p->visited_mode > 4)
+        return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2, 3, 4}", p->visited_mode);
+    if ((p->visited_mode == 2 || p->visited_mode == 3) && (async || csize > 1))
+        return fail(ANN_ERR_ARG, "the direct-mapped visited caches 2 and 3 are for the one-CTA sync kernel");
+    if (p->visited_mode == 4 && csize > 1)
+        return fail(ANN_ERR_ARG, "the set-associative visited cache is for the one-CTA kernels");
     int idbits = 1;  // bits of the largest vertex id
     while (idbits < 31 && (int64_t(1) << idbits) < x.n) ++idbits;
+    // tags per set word of the set-associative cache with 2^bits sets (0 if not even two fit)
+    auto ways_for = [&](int bits) {
+        const int fw = (idbits > bits ? idbits - bits : 0) + 1;
+        return fw <= 10 ? 3 : (fw <= 16 ? 2 : 0);
+    };
+    // auto: a set-associative cache of tags for queues of 128 or more (thousands of vertices visited:
+    // capacity and associativity pay; in the same 16 KB three ways repeat a few percent of the distances
+    // that one way repeats), full ids below (a 2^12-id cache already holds what a short search visits, and
+    // its exchange is cheaper than a CAS)
+    // (the asynchronous walkers take it at every L: a set that forgets lets a walker queue, expand and
+    // count again what another walker already saw, which changes when Algorithm 2 merges)
+    int vmode = p->visited_mode == 0 ? (csize > 1 ? 1 : (async || L >= 128) ? 4 : 3) : p->visited_mode;
+    if (vmode == 4 && ways_for(15) < 2) {
+        if (p->visited_mode == 4)
+            return fail(ANN_ERR_ARG, "visited_mode=4: ids of %d bits leave no room for two tags per set word", idbits);
+        vmode = async ? 1 : 2;
+    }
     auto slot_bytes_for = [&](int bits) {
         if (vmode != 2) return 4;
         const int tb = idbits > bits ? idbits - bits : 0;
@@ -235,18 +255,25 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     };
     int hb = p->hash_bits;
     if (hb == 0) {
-        if (many) {  // the most slots that fit in 16 KB (2^12 full ids; 2^14 one-byte tags)
+        if (many) {  // the most slots that fit in 16 KB (2^12 full ids or set words; 2^14 one-byte tags)
             hb = 12;
             for (int b = 14; b > 12; --b)
                 if ((1 << b) * slot_bytes_for(b) <= (16 << 10)) {
                     hb = b;
                     break;
                 }
+            while (vmode == 4 && ways_for(hb) < 2) ++hb;  // more sets leave more bits per tag
+        } else if (vmode == 4) {  // 2^13 sets hold 24,576 tags in 32 KB; 2^14 for long queues or heavy steps
+            hb = heavy ? 14 : 13;
+            while (ways_for(hb) < 2) ++hb;
         } else {
             hb = heavy ? 14 : (M * x.R >= 1024 ? 13 : 12);
         }
     }
     if (hb < 8 || hb > 15) return fail(ANN_ERR_ARG, "hash_bits=%d outside [8, 15]", hb);
+    if (vmode == 4 && ways_for(hb) < 2)
+        return fail(ANN_ERR_ARG, "visited_mode=4 with 2^%d sets: ids of %d bits leave no room for two tags", hb,
+                    idbits);
 
     ann::SearchArgs &a = plan->a;
     memset(&a, 0, sizeof(a));
@@ -278,6 +305,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (p->l2_prefetch < 0 || p->l2_prefetch > 2)
         return fail(ANN_ERR_ARG, "l2_prefetch=%d not in {0, 1, 2}", p->l2_prefetch);
     a.l2_prefetch = p->l2_prefetch != 2;
+    // neighbour groups serve the one-CTA sync kernel (the other kernels read every row by its id)
+    a.hot_slot = (!async && csize == 1 && x.n_hot > 0) ? x.hot_slot : nullptr;
+    a.group_prefetch = x.group_prefetch;
     {
         const int tl = p->team_lanes;
         if (!(tl == -1 || tl == 0 || (tl > 0 && tl <= 32 && (tl & (tl - 1)) == 0)))
@@ -307,9 +337,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.Lcap = L;
     int need = M * x.R;
     if (a.rerank && L > need) need = L;
-    if (!async && csize == 1) {  // the warps' fresh-id lists live in the candidate segment (two ids per entry)
+    if (!async && csize == 1) {  // the warps' fresh lists live in the candidate segment
         const int nw = threads / 32;
-        const int fresh_entries = (nw * ((M + nw - 1) / nw) * x.R + 1) / 2;
+        const int fresh_entries = nw * ((M + nw - 1) / nw) * x.R;  // one (id, row) pair per entry
         if (fresh_entries > need) need = fresh_entries;
     }
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);
@@ -323,7 +353,10 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     // an automatic visited table shrinks until the layout fits (it may then forget more often)
     while (p->hash_bits == 0 && smem > max_dyn_smem() && a.hash_bits > 10) smem = smem_for(--a.hash_bits);
     a.slot_bytes = slot_bytes_for(a.hash_bits);
-    a.tag_bits = a.slot_bytes < 4 && idbits > a.hash_bits ? idbits - a.hash_bits : 0;
+    a.tag_bits = (a.slot_bytes < 4 || vmode == 4) && idbits > a.hash_bits ? idbits - a.hash_bits : 0;
+    a.ways = vmode == 4 ? ways_for(a.hash_bits) : 0;
+    if (vmode == 4 && a.ways < 2)
+        return fail(ANN_ERR_ARG, "visited_mode=4: the set words do not fit two tags at 2^%d sets", a.hash_bits);
     a.sync_lay = ann::sync_layout(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, M, a.slot_bytes, threads / 32);
     if (smem > max_dyn_smem())
         return fail(ANN_ERR_ARG, "shared memory %d B exceeds the device limit %d B (lower L, M or hash_bits)",
@@ -440,6 +473,87 @@ int ann_index_get_info(const ann_index *index, ann_index_info *info) {
     info->has_f32 = x.base32 != nullptr;
     info->entry = x.entry;
     info->device_bytes = x.device_bytes;
+    info->n_hot = x.n_hot;
+    return ANN_OK;
+}
+
+int ann_index_group_neighbors(ann_index *index, float hot_fraction, int32_t prefetch) {
+    if (!index) return fail(ANN_ERR_ARG, "index is NULL");
+    if (!(hot_fraction >= 0.f && hot_fraction <= 0.05f))
+        return fail(ANN_ERR_ARG, "hot_fraction=%g outside [0, 0.05]", (double)hot_fraction);
+    if (prefetch != 0 && prefetch != 1) return fail(ANN_ERR_ARG, "prefetch=%d not in {0, 1}", prefetch);
+    ann::IndexData &x = index->d;
+    int dev = 0;
+    ANN_CUDA(cudaGetDevice(&dev));
+    if (dev != x.device) return fail(ANN_ERR_STATE, "current device %d is not the index's device %d", dev, x.device);
+    const int64_t H = (int64_t)std::llround((double)hot_fraction * (double)x.n);
+    if ((uint64_t)x.n + (uint64_t)H * (uint64_t)x.R >= (1ull << 32))
+        return fail(ANN_ERR_ARG, "n + hot vertices * R must stay below 2^32 rows");
+    ANN_CUDA(cudaDeviceSynchronize());
+    const int64_t es = ann::storage_bytes(x.storage), row_bytes = (int64_t)x.d_pad * es;
+    if (H == 0) {  // no groups: the search reads every row by its id (the spare rows stay allocated)
+        cudaFree(x.hot_slot);
+        x.hot_slot = nullptr;
+        x.n_hot = 0;
+        return ANN_OK;
+    }
+    // in-degrees, then the H vertices with the most in-edges (ties: the smaller id)
+    std::vector<int32_t> deg(x.n);
+    {
+        int32_t *ddeg = nullptr;
+        ANN_CUDA(cudaMalloc(&ddeg, (size_t)x.n * 4));
+        cudaError_t e = cudaMemset(ddeg, 0, (size_t)x.n * 4);
+        if (e == cudaSuccess) e = ann::launch_count_in_degree(x.adj, x.n * (int64_t)x.R, ddeg, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(deg.data(), ddeg, (size_t)x.n * 4, cudaMemcpyDeviceToHost);
+        cudaFree(ddeg);
+        if (e != cudaSuccess) return cuda_fail(e, "in-degree");
+    }
+    std::vector<int32_t> order(x.n);
+    for (int64_t i = 0; i < x.n; ++i) order[i] = (int32_t)i;
+    auto hotter = [&](int32_t a, int32_t b) { return deg[a] > deg[b] || (deg[a] == deg[b] && a < b); };
+    std::nth_element(order.begin(), order.begin() + (H - 1), order.end(), hotter);
+    std::sort(order.begin(), order.begin() + H);  // groups in id order
+    std::vector<int32_t> slot(x.n, -1);
+    for (int64_t s = 0; s < H; ++s) slot[order[s]] = (int32_t)s;
+    // a base (and scale) buffer with room for the groups, the first n rows copied over
+    const int64_t rows = x.n + H * x.R;
+    unsigned char *nb = nullptr;
+    float *nsc = nullptr;
+    int32_t *dhot = nullptr, *dslot = nullptr;
+    auto undo = [&](int code) {
+        cudaFree(nb);
+        cudaFree(nsc);
+        cudaFree(dhot);
+        cudaFree(dslot);
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&nb, (size_t)rows * row_bytes)) != cudaSuccess) return undo(cuda_fail(e, "cudaMalloc(groups)"));
+    if (x.scales && (e = cudaMalloc(&nsc, (size_t)rows * 4)) != cudaSuccess) return undo(cuda_fail(e, "cudaMalloc(scales)"));
+    if ((e = cudaMalloc(&dhot, (size_t)H * 4)) != cudaSuccess) return undo(cuda_fail(e, "cudaMalloc(hot)"));
+    if ((e = cudaMalloc(&dslot, (size_t)x.n * 4)) != cudaSuccess) return undo(cuda_fail(e, "cudaMalloc(hot_slot)"));
+    e = cudaMemcpy(nb, x.base, (size_t)x.n * row_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && nsc) e = cudaMemcpy(nsc, x.scales, (size_t)x.n * 4, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dhot, order.data(), (size_t)H * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dslot, slot.data(), (size_t)x.n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = ann::launch_fill_groups(nb, nsc, x.adj, dhot, H, x.R, x.n, (int32_t)row_bytes, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(dhot);
+    dhot = nullptr;
+    if (e != cudaSuccess) return undo(cuda_fail(e, "neighbour groups"));
+    const bool alias32 = !x.owns_base32 && x.base32 == reinterpret_cast<float *>(x.base);
+    const int64_t old_rows = x.n + x.n_hot * x.R;
+    cudaFree(x.base);
+    cudaFree(x.scales);
+    cudaFree(x.hot_slot);
+    x.base = nb;
+    x.scales = nsc;
+    x.hot_slot = dslot;
+    if (alias32) x.base32 = reinterpret_cast<float *>(nb);
+    x.device_bytes += (rows - old_rows) * row_bytes + (nsc ? (rows - old_rows) * 4 : 0) +
+                      (old_rows == x.n ? x.n * 4 : 0);
+    x.n_hot = H;
+    x.group_prefetch = prefetch;
     return ANN_OK;
 }
 
@@ -508,6 +622,7 @@ int ann_search_describe(const ann_index *index, int64_t nq, int32_t k, int32_t L
     out->cluster = plan.cluster;
     out->mode = plan.mode;
     out->visited_slot_bytes = plan.a.slot_bytes;
+    out->visited_ways = plan.a.ways;
     return ANN_OK;
 }
 

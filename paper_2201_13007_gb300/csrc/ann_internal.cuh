@@ -33,6 +33,11 @@ struct IndexData {
     // staging for ann_search_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // neighbour groups (Sec. 4.4): base (and scales) hold n_hot * R more rows after the n vertices' rows,
+    // the neighbours of each hot vertex in adjacency order; hot_slot[v] = v's group or -1
+    int32_t *hot_slot = nullptr;
+    int64_t n_hot = 0;
+    int32_t group_prefetch = 0;  // 0 = one bulk prefetch of a hot vertex's block; 1 = the fresh rows only
     // device work counters of persistent grids: one slot (its own 128-byte line) per stream that
     // searches the index, so persistent searches on different streams never share a counter
     int *work_counter = nullptr;
@@ -49,8 +54,9 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Shared memory of the one-CTA sync kernel with nw warps. The cand segment
-// holds each warp's fresh ids during a step (nw * ceil(Mcap / nw) * R uint32,
-// which the host guarantees fit in Ccap entries) and sort output after it;
+// holds each warp's fresh (id, row) pairs during a step (nw * ceil(Mcap /
+// nw) * R of them, one per 8-byte entry; the host makes Ccap at least that)
+// and sort output after it;
 // act holds each warp's selected vertices and their queue positions.
 __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
                                                   int slot_bytes, int nw) {
@@ -88,8 +94,11 @@ struct SearchArgs {
     int32_t hash_bits;
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
     int32_t slot_bytes;    // direct-mapped slot: 4 = a full id; 1 or 2 = a tag (the hashed id's bits below the index)
-    int32_t tag_bits;      // bits of the tag when slot_bytes < 4
-    int32_t l2_prefetch;   // 1 = bulk L2 prefetch of each candidate row once it passes the visited filter
+    int32_t tag_bits;      // bits of the tag when slot_bytes < 4 or ways > 0
+    int32_t ways;          // set-associative cache: tags per 32-bit set word (2 or 3); 0 = another form
+    int32_t l2_prefetch;   // 1 = L2 prefetch of each candidate row once it passes the visited filter
+    const int32_t *hot_slot; // neighbour groups: n entries, the group of a hot vertex or -1 (nullptr: none)
+    int32_t group_prefetch;  // 0 = one bulk prefetch per hot vertex's block; 1 = the fresh rows only
     int32_t team_lanes;    // distance gather: log2 of the lanes that share one candidate row
     int32_t team_lanes32;  // the same for the FP32 rows of the re-rank
     int64_t *out_ids;
@@ -161,5 +170,8 @@ cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, v
                           float *scales, cudaStream_t stream);
 cudaError_t launch_count_bad_adj(const int32_t *adj, int64_t count, int64_t n, unsigned long long *bad,
                                  cudaStream_t stream);
+cudaError_t launch_count_in_degree(const int32_t *adj, int64_t count, int32_t *deg, cudaStream_t stream);
+cudaError_t launch_fill_groups(unsigned char *rows, float *scales, const int32_t *adj, const int32_t *hot,
+                               int64_t n_hot, int32_t R, int64_t n, int32_t row_bytes, cudaStream_t stream);
 
 }  // namespace ann

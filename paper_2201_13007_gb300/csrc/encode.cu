@@ -1,6 +1,7 @@
 // encode.cu -- index-build kernels: FP32 rows -> stored rows (FP32, BF16,
 // FP16, or FP8 E4M3 with a per-vector scale max|x|/448), zero padded to
-// d_pad elements; and a range check of the adjacency ids.
+// d_pad elements; a range check of the adjacency ids; in-degrees and the
+// neighbour-group copies of ann_index_group_neighbors.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -68,6 +69,45 @@ __global__ void count_bad_adj(const int32_t *__restrict__ adj, int64_t count, in
 cudaError_t launch_count_bad_adj(const int32_t *adj, int64_t count, int64_t n, unsigned long long *bad,
                                  cudaStream_t stream) {
     count_bad_adj<<<1024, 256, 0, stream>>>(adj, count, n, bad);
+    return cudaGetLastError();
+}
+
+// In-degree of every vertex: deg[u] += 1 for each edge v -> u.
+__global__ void count_in_degree(const int32_t *__restrict__ adj, int64_t count, int32_t *__restrict__ deg) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = adj[i];
+        if (u >= 0) atomicAdd(deg + u, 1);
+    }
+}
+
+cudaError_t launch_count_in_degree(const int32_t *adj, int64_t count, int32_t *deg, cudaStream_t stream) {
+    count_in_degree<<<1024, 256, 0, stream>>>(adj, count, deg);
+    return cudaGetLastError();
+}
+
+// Neighbour groups: row n + s * R + r of rows[] becomes a copy of the row of
+// the r-th neighbour of hot vertex hot[s] (zeros, scale 1, for a -1 slot).
+// One warp per group row, 16-byte copies.
+__global__ void fill_groups(unsigned char *__restrict__ rows, float *__restrict__ scales,
+                            const int32_t *__restrict__ adj, const int32_t *__restrict__ hot, int64_t n_hot,
+                            int32_t R, int64_t n, int32_t row_bytes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (g >= n_hot * R) return;
+    const int64_t s = g / R, r = g - s * R;
+    const int32_t u = adj[(size_t)hot[s] * R + r];
+    uint4 *dst = reinterpret_cast<uint4 *>(rows + (size_t)(n + g) * row_bytes);
+    const uint4 *src = reinterpret_cast<const uint4 *>(rows + (size_t)(u >= 0 ? u : 0) * row_bytes);
+    for (int c = lane; c < row_bytes / 16; c += 32) dst[c] = u >= 0 ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+    if (scales && lane == 0) scales[n + g] = u >= 0 ? scales[u] : 1.0f;
+}
+
+cudaError_t launch_fill_groups(unsigned char *rows, float *scales, const int32_t *adj, const int32_t *hot,
+                               int64_t n_hot, int32_t R, int64_t n, int32_t row_bytes, cudaStream_t stream) {
+    const int64_t warps = n_hot * R;
+    if (warps == 0) return cudaSuccess;
+    fill_groups<<<(unsigned)((warps + 7) / 8), 256, 0, stream>>>(rows, scales, adj, hot, n_hot, R, n, row_bytes);
     return cudaGetLastError();
 }
 

@@ -5,21 +5,24 @@
 //   deal   the unchecked entries of the global queue S go round-robin, by
 //          rank, to the M active walkers' private queues; checked entries
 //          stay in S;
-//   walk   each active warp runs best-first search on its private queue on
-//          its own (expand the first unchecked entry, insert the unvisited
-//          neighbours, resize to L), sharing one visited table with the other
-//          walkers (shared-memory CAS, no ordering between walkers: the
-//          loosely synchronised visiting map of Sec. 4.4). After every
-//          expansion it publishes its update position (best rank at which a
-//          new candidate landed, L if none) and fences. The checker walker
-//          (round robin) evaluates mean(U) >= L * R (Algorithm 2) and raises
-//          doMerge; every walker stops at its next expansion boundary, or when
-//          its private queue has nothing unchecked;
+//   walk   in sub-steps: in each, every active walker (warp) with an
+//          unchecked entry expands the first one of its private queue
+//          (insert the unvisited neighbours, resize to L), sharing one
+//          visited set with the other walkers (shared-memory CAS, no
+//          ordering between walkers within a sub-step: the loosely
+//          synchronised visiting map of Sec. 4.4), and records its update
+//          position (best rank at which a new candidate landed, L if none).
+//          A CTA barrier ends the sub-step; then every thread evaluates the
+//          same Algorithm 2 test for the checker walker (round robin): if the
+//          checker expanded in this sub-step and mean(U) >= L * R, or if no
+//          walker expanded, the walk ends. Sub-steps are cheap on a GPU (one
+//          CTA barrier), so the walkers advance in lock-step as in the
+//          oracle's reading of Algorithm 3, and every update position the
+//          checker averages is from the same sub-step;
 //   merge  the private queues merge into S (dedupe by id, checked wins),
 //          S is resized to L, and M doubles while M < M_max.
 // The search ends when a deal finds no unchecked entry. No warp ever waits on
-// another warp; the only cross-warp communication is the visited table, the
-// update positions and the doMerge flag, all in shared memory.
+// another except at CTA barriers that every warp reaches.
 #include "search_common.cuh"
 
 namespace ann {
@@ -31,7 +34,7 @@ struct AsyncCtrl {
     int chunk_tot[64];
     int merged_len;
     int hash_count;
-    int tmp;
+    int walk[2][32];  // per sub-step parity and walker: (update position << 1) | expanded-in-this-sub-step
 };
 
 __host__ __device__ inline int async_smem_bytes(int qfloats, int Lcap, int walkers, int hash_bits, int *offs) {
@@ -44,8 +47,16 @@ __host__ __device__ inline int async_smem_bytes(int qfloats, int Lcap, int walke
     offs[5] = o; o += align16(Lcap > 32 ? Lcap : 32);       // dup flags
     offs[6] = o; o += align16((1 << hash_bits) * 4);        // visited table
     offs[7] = o; o += align16(walkers * 4);                 // private queue lengths
-    offs[8] = o; o += align16(walkers * 4);                 // update positions
     return o;
+}
+
+// One insert into the walkers' shared visited set: the set-associative cache
+// of tags (a.ways > 0; it forgets a vertex only when a fourth one enters its
+// set) or an open-addressing table reset when half full. 0 = seen before.
+__device__ __forceinline__ int async_visit(uint32_t *table, const SearchArgs &a, uint32_t id) {
+    if (a.ways == 3) return visited_assoc<3>(table, a.hash_bits, a.tag_bits, id);
+    if (a.ways == 2) return visited_assoc<2>(table, a.hash_bits, a.tag_bits, id);
+    return visited_insert(table, a.hash_bits, id);
 }
 
 template <int NT, int STORE>
@@ -53,9 +64,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
     constexpr int T = NT / 32;  // walkers
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ AsyncCtrl ctl;
-    __shared__ volatile int do_merge;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int off[9];
+    int off[8];
     async_smem_bytes(a.qfloats, a.Lcap, T, a.hash_bits, off);
     float *qv = reinterpret_cast<float *>(smem + off[0]);
     entry_t *Sa = reinterpret_cast<entry_t *>(smem + off[1]);
@@ -65,7 +75,6 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
     unsigned char *dup = smem + off[5];
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + off[6]);
     int *lsn = reinterpret_cast<int *>(smem + off[7]);
-    volatile int *U = reinterpret_cast<volatile int *>(smem + off[8]);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
     const int Lcap = a.Lcap;
@@ -102,7 +111,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
 
         const float *qg = a.queries + (size_t)qi * a.d;
         for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
-        for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
+        for (int i = tid; i < H; i += NT) table[i] = a.ways ? 0u : kEmptySlot;
         entry_t *CW0 = CWall;
         if (tid == 0) CW0[0] = (entry_t)(uint32_t)a.entry;
         __syncthreads();
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
         __syncthreads();
         if (tid == 0) {
             Sa[0] = CW0[0];
-            visited_insert(table, a.hash_bits, (uint32_t)a.entry);
+            async_visit(table, a, (uint32_t)a.entry);
             ctl.hash_count = 1;
         }
         __syncthreads();
@@ -165,11 +174,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
                 }
             }
             const int nactive = nun < M ? nun : M;
-            if (tid < T) {
-                lsn[tid] = tid < nactive ? (nun - tid + M - 1) / M : 0;
-                U[tid] = 0;
-            }
-            if (tid == 0) do_merge = 0;
+            if (tid < T) lsn[tid] = tid < nactive ? (nun - tid + M - 1) / M : 0;
             __syncthreads();
             {
                 entry_t *t = S;
@@ -179,96 +184,102 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
             slen = slen - nun;
             const int chk = (int)(checker % nactive);
 
-            // ---------------- walkers
+            // ---------------- walkers, in lock-step sub-steps (one CTA barrier each)
             bool raised = false;
-            if (warp < nactive) {
+            {
                 entry_t *Q = LSall + (size_t)warp * Lcap;
                 entry_t *cw = CWall + warp * 32;
-                int ql = lsn[warp];
-                for (;;) {
-                    if (__any_sync(kFull, do_merge != 0)) break;
-                    int idx = -1;
-                    for (int b = 0; b < ql; b += 32) {
-                        const int i = b + lane;
-                        const bool un = i < ql && !(Q[i] & kChecked);
-                        const unsigned bal = __ballot_sync(kFull, un);
-                        if (bal) {
-                            idx = b + __ffs(bal) - 1;
-                            break;
-                        }
-                    }
-                    if (idx < 0) break;  // private queue exhausted
-                    const entry_t ev = Q[idx];
-                    __syncwarp();
-                    if (lane == 0) Q[idx] = ev | kChecked;
-                    __syncwarp();
-                    const uint32_t v = entry_id(ev);
-                    w_exp++;
-                    int upos = L;
-                    for (int r0 = 0; r0 < R; r0 += 32) {
-                        const int r = r0 + lane;
-                        const int u = r < R ? __ldg(a.adj + (size_t)v * R + r) : -1;
-                        const bool fresh = u >= 0 && visited_insert(table, a.hash_bits, (uint32_t)u) != 0;
-                        const unsigned bal = __ballot_sync(kFull, fresh);
-                        const int nf = __popc(bal);
-                        if (fresh) cw[__popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
-                        __syncwarp();
-                        if (nf == 0) continue;
-                        if (lane == 0) atomicAdd(&ctl.hash_count, nf);
-                        w_evals += nf;
-                        warp_compute_keys<STORE>(a.base, a.scales, a.d_pad, a.metric, qv, cw, nf);
-                        entry_t e = lane < nf ? cw[lane] : kEmptyEntry;
-                        e = warp_sort32(e);
-                        // drop ids already in this private queue (or repeated in this row)
-                        const entry_t prev = __shfl_up_sync(kFull, e, 1);
-                        int pq = lane < nf ? count_below(Q, ql, e) : ql;
-                        const bool dupl = lane < nf && ((pq < ql && (Q[pq] & kMask) == e) || (lane > 0 && prev == e));
-                        const bool keep = lane < nf && !dupl;
-                        const unsigned kb = __ballot_sync(kFull, keep);
-                        const int nk = __popc(kb);
-                        __syncwarp();
-                        if (keep) cw[__popc(kb & ((1u << lane) - 1u))] = e;
-                        __syncwarp();
-                        // target ranks of the kept candidates (against the old queue)
-                        entry_t cnew = lane < nk ? cw[lane] : kEmptyEntry;
-                        const int pnew = lane < nk ? lane + count_below(Q, ql, cnew) : L;
-                        // move existing entries back to front
-                        for (int b = ((ql + 31) / 32 - 1) * 32; b >= 0; b -= 32) {
+                int ql = warp < nactive ? lsn[warp] : 0;
+                int upos_w = 0;  // this walker's update position (U is reset to 0 at each deal)
+                for (int sub = 0;; ++sub) {
+                    const int par = sub & 1;
+                    bool expanded = false;
+                    if (warp < nactive) {
+                        int idx = -1;
+                        for (int b = 0; b < ql; b += 32) {
                             const int i = b + lane;
-                            const entry_t ei = i < ql ? Q[i] : 0ull;
-                            const int pi = i < ql ? i + count_below(cw, nk, ei & kMask) : L;
-                            __syncwarp();
-                            if (i < ql && pi < L) Q[pi] = ei;
-                            __syncwarp();
+                            const bool un = i < ql && !(Q[i] & kChecked);
+                            const unsigned bal = __ballot_sync(kFull, un);
+                            if (bal) {
+                                idx = b + __ffs(bal) - 1;
+                                break;
+                            }
                         }
-                        if (lane < nk && pnew < L) Q[pnew] = cnew;
-                        __syncwarp();
-                        ql = min(L, ql + nk);
-                        const int best = __shfl_sync(kFull, pnew, 0);
-                        if (nk > 0 && best < upos) upos = best;
-                    }
-                    // publish the update position, then let the checker look
-                    if (lane == 0) {
-                        U[warp] = upos;
-                        __threadfence_block();
-                    }
-                    __syncwarp();
-                    if (warp == chk) {
-                        const int uv = lane < nactive ? U[lane] : 0;
-                        int sum = uv;
-                        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-                        if ((float)sum / (float)nactive >= threshold) {
-                            if (lane == 0) do_merge = 1;
-                            raised = true;
-                            break;
+                        if (idx >= 0) {
+                            expanded = true;
+                            const entry_t ev = Q[idx];
+                            __syncwarp();
+                            if (lane == 0) Q[idx] = ev | kChecked;
+                            __syncwarp();
+                            const uint32_t v = entry_id(ev);
+                            w_exp++;
+                            int upos = L;
+                            for (int r0 = 0; r0 < R; r0 += 32) {
+                                const int r = r0 + lane;
+                                const int u = r < R ? __ldg(a.adj + (size_t)v * R + r) : -1;
+                                const bool fresh = u >= 0 && async_visit(table, a, (uint32_t)u) != 0;
+                                const unsigned bal = __ballot_sync(kFull, fresh);
+                                const int nf = __popc(bal);
+                                if (fresh) cw[__popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
+                                __syncwarp();
+                                if (nf == 0) continue;
+                                if (lane == 0) atomicAdd(&ctl.hash_count, nf);
+                                w_evals += nf;
+                                warp_compute_keys<STORE>(a.base, a.scales, a.d_pad, a.metric, qv, cw, nf);
+                                entry_t e = lane < nf ? cw[lane] : kEmptyEntry;
+                                e = warp_sort32(e);
+                                // drop ids already in this private queue (or repeated in this row)
+                                const entry_t prev = __shfl_up_sync(kFull, e, 1);
+                                int pq = lane < nf ? count_below(Q, ql, e) : ql;
+                                const bool dupl =
+                                    lane < nf && ((pq < ql && (Q[pq] & kMask) == e) || (lane > 0 && prev == e));
+                                const bool keep = lane < nf && !dupl;
+                                const unsigned kb = __ballot_sync(kFull, keep);
+                                const int nk = __popc(kb);
+                                __syncwarp();
+                                if (keep) cw[__popc(kb & ((1u << lane) - 1u))] = e;
+                                __syncwarp();
+                                // target ranks of the kept candidates (against the old queue)
+                                entry_t cnew = lane < nk ? cw[lane] : kEmptyEntry;
+                                const int pnew = lane < nk ? lane + count_below(Q, ql, cnew) : L;
+                                // move the existing entries at or after the first insertion point, back to front
+                                const int p0 = __shfl_sync(kFull, pnew, 0);
+                                for (int b = ((ql + 31) / 32 - 1) * 32; b >= 0 && b + 32 > p0 - 0; b -= 32) {
+                                    const int i = b + lane;
+                                    const entry_t ei = i < ql ? Q[i] : 0ull;
+                                    const int pi = i < ql ? i + count_below(cw, nk, ei & kMask) : L;
+                                    __syncwarp();
+                                    if (i < ql && pi < L && pi != i) Q[pi] = ei;
+                                    __syncwarp();
+                                }
+                                if (lane < nk && pnew < L) Q[pnew] = cnew;
+                                __syncwarp();
+                                ql = min(L, ql + nk);
+                                if (nk > 0 && p0 < upos) upos = p0;
+                            }
+                            upos_w = upos;
                         }
+                    }
+                    if (lane == 0 && warp < T) ctl.walk[par][warp] = (upos_w << 1) | (expanded ? 1 : 0);
+                    __syncthreads();  // the sub-step is over: every walker's word for it is written
+                    // every thread evaluates the same test (Algorithm 2 for the checker; none expanded = all idle)
+                    bool any = false;
+                    int sum = 0;
+                    for (int w2 = 0; w2 < nactive; ++w2) {
+                        const int wd = ctl.walk[par][w2];
+                        any |= (wd & 1) != 0;
+                        sum += wd >> 1;
+                    }
+                    if (!any) break;
+                    if ((ctl.walk[par][chk] & 1) && (float)sum / (float)nactive >= threshold) {
+                        raised = true;
+                        break;
                     }
                 }
-                if (lane == 0) lsn[warp] = ql;
+                if (warp < nactive && lane == 0) lsn[warp] = ql;
             }
-            if (warp == chk && lane == 0) ctl.tmp = raised ? 1 : 0;
             __syncthreads();
-            if (ctl.tmp) checker++;
+            if (raised) checker++;
             // ---------------- merge the private queues into S
             for (int w = 0; w < nactive; ++w) {
                 slen = block_merge_dedupe<NT>(S, slen, LSall + (size_t)w * Lcap, lsn[w], L, Sn, dup,
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
             gsteps++;
             if (M < Mmax) M = min(2 * M, Mmax);
             // forget the visited table when half full (keep the queued ids)
-            if (ctl.hash_count * 2 > H) {
+            if (!a.ways && ctl.hash_count * 2 > H) {
                 for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
                 __syncthreads();
                 for (int i = tid; i < slen; i += NT) visited_insert(table, a.hash_bits, entry_id(S[i]));
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
 }
 
 int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits) {
-    int off[9];
+    int off[8];
     return async_smem_bytes(qfloats, Lcap, walkers, hash_bits, off);
 }
 

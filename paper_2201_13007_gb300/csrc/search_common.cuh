@@ -119,12 +119,22 @@ template <> struct Chunk<ANN_STORE_E4M3> {
     }
 };
 
-// Ask for one row (bytes a multiple of 16, 16-byte aligned start) to be
-// brought into L2 by the bulk-copy unit; no completion is tracked and no
-// register is held, so every row of a step can be in flight at once.
+// Ask L2 for one row: one prefetch.global.L2 per 128-byte line it touches.
+// No completion is tracked and no register is held, so every row of a step
+// can be in flight at once. Each lane names its own row: a bulk prefetch
+// (cp.async.bulk.prefetch.L2) takes a warp-uniform address, so rows that
+// differ per lane would be issued one lane at a time.
 __device__ __forceinline__ void prefetch_row_l2(const void *rows, uint32_t row_bytes, uint32_t id) {
-    const char *p = static_cast<const char *>(rows) + (size_t)id * row_bytes;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(row_bytes)
+    const uintptr_t p = reinterpret_cast<uintptr_t>(rows) + (size_t)id * row_bytes;
+    const uintptr_t end = p + row_bytes;
+    for (uintptr_t a = p & ~uintptr_t(127); a < end; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
+// Ask L2 for one contiguous range (16-byte aligned start, bytes a multiple
+// of 16) with a single bulk prefetch. The address must be the same in every
+// lane that executes it; callers issue it from one lane.
+__device__ __forceinline__ void prefetch_range_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
                  : "memory");
 }
 
@@ -331,6 +341,42 @@ __device__ __forceinline__ int visited_tag(uint32_t *table, int bits, int tag_bi
         if (cur == tag) return 0;
         const uint32_t prev = atomicCAS(wp, old, (old & ~(MASK << sh)) | (tag << sh));
         if (prev == old) return cur == 0u ? 1 : 3;
+        old = prev;
+    }
+    return 3;
+}
+
+// Set-associative visited cache: 2^bits sets of one 32-bit word, each word
+// holding W fields of tag_bits + 1 bits (a tag plus one; 0 = an empty way),
+// the newest in the lowest field. As in visited_tag, h = (id * odd constant)
+// mod 2^b with b = bits + tag_bits >= the bits of any id is a bijection: the
+// top `bits` of h choose the set and the low tag_bits are the tag, so (set,
+// tag) names exactly one id and the cache never claims a vertex it did not
+// see. An insert that finds the tag in one of the W fields returns 0; else
+// the word shifts up by one field (first in, first out: the oldest way falls
+// out) and the tag enters the lowest field, returning 1 if no vertex fell out
+// and 3 if one was forgotten. The word is replaced with a CAS (a lost race
+// re-reads the word; after 32 losses the vertex is treated as fresh, which
+// only costs a repeated distance).
+template <int W>
+__device__ __forceinline__ int visited_assoc(uint32_t *table, int bits, int tag_bits, uint32_t id) {
+    const int b = bits + tag_bits;
+    uint32_t h = id * 0x9E3779B1u;
+    if (b < 32) h &= (1u << b) - 1u;
+    const uint32_t set = h >> tag_bits;
+    const uint32_t tag = (h & ((1u << tag_bits) - 1u)) + 1u;
+    const int fw = tag_bits + 1;  // W * fw <= 32 (host checks)
+    const uint32_t fmask = (1u << fw) - 1u;
+    const uint32_t wmask = W * fw >= 32 ? 0xFFFFFFFFu : (1u << (W * fw)) - 1u;
+    uint32_t *wp = table + set;
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(wp);
+    for (int it = 0; it < 32; ++it) {
+        bool seen = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) seen |= ((old >> (w * fw)) & fmask) == tag;
+        if (seen) return 0;
+        const uint32_t prev = atomicCAS(wp, old, ((old << fw) | tag) & wmask);
+        if (prev == old) return ((old >> ((W - 1) * fw)) & fmask) ? 3 : 1;
         old = prev;
     }
     return 3;
@@ -635,6 +681,140 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
     }
     __syncthreads();
     return min(L, qlen + ncl);
+}
+
+// ------------------------------------------------------- warp row gathers
+// Keys of the nf candidates fr[0..nf) (one warp): fr[c].x is the vertex id
+// and fr[c].y the row that holds its vector (the id itself, or a row of a
+// neighbour group). Teams of 2^lts lanes per row; each lane walks its own
+// 16-byte chunks of the row, G of them in flight. Candidates below `limit`
+// are appended to out[] through the shared counter *out_n. No barrier.
+template <int STORE, int G, bool L2>
+__device__ __forceinline__ void warp_keys_append_m(const void *rows, const float *scales, uint32_t cpr,
+                                                   const float *qv, const uint2 *fr, int nf, int lts,
+                                                   entry_t limit, entry_t *out, int *out_n) {
+    constexpr int EPC = Chunk<STORE>::kElems;
+    const int lane = threadIdx.x & 31;
+    const int ts = 1 << lts, rpw = 32 >> lts;
+    const int team = lane >> lts, tl = lane & (ts - 1);
+    constexpr bool l2 = L2;
+    const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
+    for (int c0 = 0; c0 < nf; c0 += rpw) {
+        const int c = c0 + team;
+        const bool valid = c < nf;
+        const uint2 f = valid ? fr[c] : make_uint2(0u, 0u);
+        const uint32_t id = f.x;
+        const float sc = (STORE == ANN_STORE_E4M3 && valid) ? __ldg(scales + f.y) : 1.f;
+        const uint4 *rp = rbase + (size_t)f.y * cpr;
+        float2 acc = make_float2(0.f, 0.f);
+        if (valid) {
+            for (uint32_t ch0 = tl; ch0 < cpr; ch0 += ts * G) {
+                uint4 v[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) v[g] = ld_row_chunk(rp + ch0 + g * ts);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (ch0 + g * ts < cpr) Chunk<STORE>::add(acc, v[g], qv + (ch0 + g * ts) * EPC, sc, l2);
+            }
+        }
+        float r = acc.x + acc.y;
+        for (int off = ts >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+        const entry_t e = pack_entry(l2 ? r : -r, id);
+        const bool keep = tl == 0 && valid && e < limit;
+        const unsigned bal = __ballot_sync(kFull, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
+    }
+}
+
+// The same contract as warp_keys_append_m for rows of exactly CPL << LTS
+// chunks: the team size, the chunks each lane reads and the rounds of G
+// loads in flight are compile-time constants, so the gather has no bounds
+// test per chunk and no runtime shift or loop count. The candidates are the
+// (id, row) pairs fr[], or, when list is given, the ids in the low words of
+// list[] (each the row of its own vector). Candidates c_begin,
+// c_begin + c_step, ... in passes of 32 >> LTS; a lane past the end of the
+// list re-reads a valid row and its key is dropped.
+template <int STORE, bool L2, int LTS, int CPL, int G>
+__device__ __forceinline__ void warp_keys_fixed(const void *rows, const float *scales, const float *qv,
+                                                const entry_t *list, const uint2 *fr, int nf, int c_begin,
+                                                int c_step, entry_t limit, entry_t *out, int *out_n) {
+    static_assert(CPL % G == 0, "rounds of G chunks must cover the lane's chunks");
+    constexpr int EPC = Chunk<STORE>::kElems;
+    constexpr int TS = 1 << LTS, RPW = 32 >> LTS, CPR = CPL * TS;
+    const int lane = threadIdx.x & 31;
+    const int team = lane >> LTS, tl = lane & (TS - 1);
+    const uint4 *rbase = reinterpret_cast<const uint4 *>(rows) + tl;
+    const float *qt = qv + tl * EPC;
+    for (int c0 = c_begin; c0 < nf; c0 += c_step) {
+        const int c = c0 + team;
+        const bool valid = c < nf;
+        const int cc = valid ? c : c0;
+        uint32_t id, row;
+        if (list) {
+            id = row = (uint32_t)(list[cc] & 0xFFFFFFFFull);
+        } else {
+            const uint2 f = fr[cc];
+            id = f.x;
+            row = f.y;
+        }
+        const float sc = STORE == ANN_STORE_E4M3 ? __ldg(scales + row) : 1.f;
+        const uint4 *rp = rbase + (size_t)row * CPR;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r0 = 0; r0 < CPL; r0 += G) {
+            uint4 v[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) v[g] = ld_row_chunk(rp + (r0 + g) * TS);
+#pragma unroll
+            for (int g = 0; g < G; ++g) Chunk<STORE>::add(acc, v[g], qt + (r0 + g) * TS * EPC, sc, L2);
+        }
+        float r = acc.x + acc.y;
+#pragma unroll
+        for (int off = TS >> 1; off > 0; off >>= 1) r += __shfl_xor_sync(kFull, r, off);
+        const entry_t e = pack_entry(L2 ? r : -r, id);
+        const bool keep = tl == 0 && valid && e < limit;
+        const unsigned bal = __ballot_sync(kFull, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(out_n, __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) out[base + __popc(bal & ((1u << lane) - 1u))] = e;
+        (void)RPW;
+    }
+}
+
+// Row shapes with a fixed-geometry gather (the workloads' 32-, 96-, 128- and
+// 960-dimensional rows at the automatic team size); other shapes take the
+// generic loop. Returns false if the shape has no fixed form.
+template <int STORE, bool L2>
+__device__ __forceinline__ bool gather_fixed(const void *rows, const float *scales, uint32_t cpr, int lts,
+                                             const float *qv, const entry_t *list, const uint2 *fr, int nf,
+                                             int c_begin, int c_step_rows, entry_t limit, entry_t *out,
+                                             int *out_n) {
+#define ANN_FIXED(LTS_, CPL_, G_)                                                                            \
+    if (lts == LTS_ && cpr == (uint32_t)((CPL_) << (LTS_))) {                                                \
+        warp_keys_fixed<STORE, L2, LTS_, CPL_, G_>(rows, scales, qv, list, fr, nf, c_begin << (5 - (LTS_)),  \
+                                                   c_step_rows << (5 - (LTS_)), limit, out, out_n);          \
+        return true;                                                                                         \
+    }
+    if constexpr (STORE == ANN_STORE_BF16 || STORE == ANN_STORE_F16) {
+        ANN_FIXED(2, 4, 4)   // 128-d
+        ANN_FIXED(2, 3, 3)   // 96-d
+        ANN_FIXED(3, 15, 5)  // 960-d
+    } else if constexpr (STORE == ANN_STORE_F32) {
+        ANN_FIXED(2, 8, 4)   // 128-d
+        ANN_FIXED(2, 6, 3)   // 96-d
+        ANN_FIXED(2, 2, 2)   // 32-d
+        ANN_FIXED(3, 30, 5)  // 960-d
+    } else {
+        ANN_FIXED(2, 15, 5)  // 960-d
+        ANN_FIXED(2, 2, 2)   // 128-d
+    }
+#undef ANN_FIXED
+    return false;
 }
 
 }  // namespace ann

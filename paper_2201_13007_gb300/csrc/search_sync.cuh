@@ -1,0 +1,491 @@
+// search_sync.cuh -- bulk-synchronous top-M best-first search, one CTA per query.
+//
+// Follows Algorithm 1 (BFiS) generalised by Sec. 4.1 to expand the top-M
+// unchecked candidates per step, with the Sec. 4.2 staged schedule (M starts
+// at M0 and doubles every t steps up to M_max). Every step ends in CTA
+// barriers, so the result is deterministic: it is the same top-L queue the
+// sequential definition produces, whatever order the warps touch it in.
+//
+// One step, inside one CTA of NW warps:
+//   select   warp 0 takes the first min(M_s, #unchecked) unchecked entries of
+//            the sorted queue by ballot + popc, starting past a prefix known to
+//            be checked; the selected vertex of rank r goes to warp r mod NW;
+//   expand   each warp reads the adjacency rows of its own selected vertices
+//            (one lane per slot, coalesced int32 rows), inserts each
+//            neighbour into the shared visited set and appends the fresh ones
+//            to its own list (one warp scan per batch of rows), asking L2 for
+//            each fresh row as it goes;
+//   distance each warp gathers its own fresh rows with teams of lanes (16-byte
+//            non-caching loads, shuffle reduction) and appends every
+//            candidate below the queue's L-th entry to the CTA's survivor
+//            list. One barrier; then each warp marks its selected entries
+//            checked;
+//   sort     the survivors by (key, id): warp sort, run-rank sort or bitonic;
+//   merge    drop survivors whose id is already queued (only possible once
+//            the visited set forgot a vertex), then a merge-path merge of the
+//            queue and the survivors, truncated to L.
+// The visited set may forget vertices (a direct-mapped cache evicts, an
+// open-addressing table is reset to the queued ids when half full); the queue
+// is then still the top-L of everything seen (a forgotten vertex that is met
+// again either duplicates a queued id, which the merge drops, or ranks below
+// the L-th entry again), so ids are unchanged and only the distance count
+// grows.
+#pragma once
+
+#include "search_common.cuh"
+
+namespace ann {
+
+struct Ctrl {
+    int ns[2];     // survivors appended in the step of this parity
+    int hash_count;
+    int do_reset;  // open addressing: the table is half full, reset it before the next select
+    int anydup;
+    int unsafe;    // 1 once the visited set may have forgotten a vertex this query
+    int first_un;  // every queue entry before this position is checked
+    int qi, k, L, Mmax;  // the query and its settings (kept here, not in registers, across the step loop)
+    int wevals;    // fresh vertices of this query, summed per warp and step
+    int sel_found, sel_last;  // the step's selection: unchecked entries seen, position of the last taken
+    // per-query counters, updated by thread 0 only
+    long long steps, expansions, evals, resets, dropped, t0;
+    long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
+};
+
+// One insert into the query's visited set, whichever form it has: 0 = was
+// present, 1 = inserted, 2 or 3 = inserted while another vertex may have been
+// forgotten (probe limit, eviction).
+__device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, uint32_t id) {
+    if (a.ways == 3) return visited_assoc<3>(table, a.hash_bits, a.tag_bits, id);
+    if (a.ways == 2) return visited_assoc<2>(table, a.hash_bits, a.tag_bits, id);
+    if (a.visited_mode == 0) return visited_insert(table, a.hash_bits, id);
+    if (a.slot_bytes == 1) return visited_tag<1>(table, a.hash_bits, a.tag_bits, id);
+    if (a.slot_bytes == 2) return visited_tag<2>(table, a.hash_bits, a.tag_bits, id);
+    return visited_exchange(table, a.hash_bits, id);
+}
+
+template <int NT, int STORE, bool L2>
+__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(const SearchArgs a) {
+    constexpr int NW = NT / 32;
+    constexpr uint32_t ES = STORE == ANN_STORE_F32 ? 4u : STORE == ANN_STORE_E4M3 ? 1u : 2u;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Ctrl ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t row_bytes = (uint32_t)a.d_pad * ES;
+    const uint32_t cpr = row_bytes / 16u;
+    const SmemLayout &lay = a.sync_lay;
+    float *qv = reinterpret_cast<float *>(smem + lay.q_off);
+    entry_t *Qa = reinterpret_cast<entry_t *>(smem + lay.q0_off);
+    entry_t *Qb = reinterpret_cast<entry_t *>(smem + lay.q1_off);
+    entry_t *cand = reinterpret_cast<entry_t *>(smem + lay.cand_off);
+    entry_t *surv = reinterpret_cast<entry_t *>(smem + lay.cand2_off);
+    unsigned char *dup = smem + lay.dup_off;
+    uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
+    const int H = 1 << a.hash_bits;
+    const int R = a.R;
+    const int SR = (R + 31) >> 5;                 // 32-lane parts per adjacency row
+    const int rows_w = (a.M + NW - 1) / NW;      // most rows one warp expands in a step
+    // this warp's selected vertices (ids, queue positions) and its fresh vertices
+    int *sel_id = reinterpret_cast<int *>(smem + lay.act_off) + warp * rows_w;
+    int *sel_pos = reinterpret_cast<int *>(smem + lay.act_off) + NW * rows_w + warp * rows_w;
+    uint2 *fresh = reinterpret_cast<uint2 *>(cand) + (size_t)warp * rows_w * R;  // (id, row) pairs
+
+    for (;;) {
+        if (tid == 0) {
+            const int item = a.persistent ? atomicAdd(a.work_counter, 1) : (int)blockIdx.x;
+            const int q = item >= a.nq ? -1 : (a.order ? a.order[item] : item);
+            ctl.qi = q;
+            if (q >= 0) {
+                ctl.k = a.k_arr ? a.k_arr[q] : a.k;
+                ctl.L = a.L_arr ? a.L_arr[q] : a.L;
+                ctl.Mmax = a.M_arr ? a.M_arr[q] : a.M;
+            }
+            ctl.wevals = 0;
+            ctl.t0 = global_ns();
+            ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
+            ctl.evals = 1;
+            ctl.unsafe = 0;
+            ctl.first_un = 0;
+            ctl.do_reset = 0;
+            ctl.ph[0] = ctl.ph[1] = ctl.ph[2] = ctl.ph[3] = 0;
+        }
+        __syncthreads();
+        const int qi = ctl.qi;
+        if (qi < 0) break;  // work list exhausted
+
+        const bool bad = ctl.k < 1 || ctl.k > a.k || ctl.L < ctl.k || ctl.L > a.L || ctl.Mmax < 1 || ctl.Mmax > a.M;
+        if (bad) {
+            for (int i = tid; i < a.k; i += NT) {
+                a.out_ids[(size_t)qi * a.k + i] = -1;
+                a.out_dists[(size_t)qi * a.k + i] = __int_as_float(0x7f800000);
+            }
+            if (tid == 0 && a.stats) {
+                ann_query_stats st = {};
+                st.steps = -1;
+                a.stats[qi] = st;
+            }
+            if (!a.persistent) break;
+            __syncthreads();
+            continue;
+        }
+
+        // query into shared memory, zero padded; clear the visited table
+        const float *qg = a.queries + (size_t)qi * a.d;
+        for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
+        {
+            const int words = (H * a.slot_bytes) >> 2;
+            const uint32_t empty = (a.slot_bytes < 4 || a.ways) ? 0u : kEmptySlot;
+            for (int i = tid; i < words; i += NT) table[i] = empty;
+        }
+        if (tid == 0) {
+            ctl.ns[0] = ctl.ns[1] = 0;
+            fresh[0] = make_uint2((uint32_t)a.entry, (uint32_t)a.entry);
+        }
+        __syncthreads();
+        // the entry point P: distance, queue = [P], visited = {P}
+        if (warp == 0)
+            warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, 1, a.team_lanes, kEmptyEntry, surv,
+                                             &ctl.ns[1]);
+        __syncthreads();
+        if (tid == 0) {
+            Qa[0] = surv[0];
+            visit_set(table, a, (uint32_t)a.entry);
+            ctl.hash_count = 1;
+            ctl.ns[1] = 0;
+        }
+        __syncthreads();
+
+        int Mcur = a.M0 < ctl.Mmax ? a.M0 : ctl.Mmax;
+        int step = 0;
+        int qlen = 1;  // the same in every thread
+        entry_t *Q = Qa, *Qn = Qb;
+        const bool prof = a.phase_cycles != nullptr;
+        if (prof && tid == 0) ctl.tmark = clock64();
+#define ANN_PHASE(i)                                   \
+    if (prof && tid == 0) {                            \
+        const long long now_ = clock64();              \
+        ctl.ph[i] += now_ - ctl.tmark;                 \
+        ctl.tmark = now_;                              \
+    }
+        for (;;) {
+            // --- forget the open-addressing table when half full (keep the queued ids);
+            // the direct-mapped cache never resets, it forgets by eviction
+            // (decided by thread 0 after the last step's distance barrier, so every thread sees one value)
+            if (ctl.do_reset) {
+                for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
+                __syncthreads();
+                for (int i = tid; i < qlen; i += NT) visited_insert(table, a.hash_bits, entry_id(Q[i]));
+                if (tid == 0) {
+                    ctl.hash_count = qlen;
+                    ctl.do_reset = 0;
+                    ctl.resets++;
+                    ctl.unsafe = 1;
+                }
+                __syncthreads();
+            }
+            const int par = step & 1;
+            // --- select: warp 0 takes the first Mcur unchecked entries (rank order) of the stable queue
+            // (entries before first_un are all checked) and hands rank r to warp r mod NW
+            int found = 0, my_rows = 0, last_pos = -1;
+            if (warp == 0) {
+                int *sid0 = reinterpret_cast<int *>(smem + lay.act_off);
+                for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
+                    const int i = b + lane;
+                    const entry_t e = i < qlen ? Q[i] : kChecked;
+                    const bool un = !(e & kChecked);
+                    const unsigned bal = __ballot_sync(kFull, un);
+                    const int r = found + __popc(bal & lt_mask);
+                    const bool take = un && r < Mcur;
+                    if (take) {
+                        sid0[(r % NW) * rows_w + r / NW] = (int)entry_id(e);
+                        sid0[NW * rows_w + (r % NW) * rows_w + r / NW] = i;
+                    }
+                    const unsigned tb = __ballot_sync(kFull, take);
+                    if (tb) last_pos = b + 31 - __clz(tb);
+                    found += __popc(bal);
+                }
+                if (lane == 0) {
+                    ctl.sel_found = found;
+                    ctl.sel_last = last_pos;
+                }
+            }
+            __syncthreads();
+            found = ctl.sel_found;
+            last_pos = ctl.sel_last;
+            const int nact = found < Mcur ? found : Mcur;
+            if (nact == 0) break;  // no unchecked vertex left (identical in every warp)
+            my_rows = nact > warp ? (nact - warp + NW - 1) / NW : 0;
+            __syncwarp();
+            ANN_PHASE(0)
+            step++;
+
+            // --- expand this warp's rows: adjacency -> visited set -> fresh list (+ L2 prefetch)
+            int nf = 0;
+            {
+                constexpr int KA = 4;  // row parts whose loads are in flight together
+                const int units = my_rows * SR;
+                for (int t0 = 0; t0 < units; t0 += KA) {
+                    int u[KA];
+                    uint32_t urow[KA];  // the row holding u's vector: u, or its copy in a neighbour group
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) {
+                        const int t = t0 + kk;
+                        u[kk] = -1;
+                        urow[kk] = 0;
+                        if (t < units) {
+                            const int j = SR == 1 ? t : t / SR;
+                            const int slot = (t - j * SR) * 32 + lane;
+                            const uint32_t v = (uint32_t)sel_id[j];
+                            if (slot < R) u[kk] = __ldg(a.adj + (size_t)v * (uint32_t)R + slot);
+                            urow[kk] = (uint32_t)u[kk];
+                            if (a.hot_slot) {
+                                // a hot vertex: its neighbours' rows lie in one block after the base rows, in
+                                // adjacency order; one bulk prefetch (from one lane) asks L2 for the block
+                                const int hs = __ldg(a.hot_slot + v);
+                                if (hs >= 0) {
+                                    const uint32_t r0 = (uint32_t)a.n + (uint32_t)hs * (uint32_t)R;
+                                    urow[kk] = r0 + (uint32_t)slot;
+                                    if (lane == 0 && a.l2_prefetch && slot == lane && a.group_prefetch == 0)
+                                        prefetch_range_l2(static_cast<const char *>(a.base) + (size_t)r0 * row_bytes,
+                                                          (uint32_t)R * row_bytes);
+                                }
+                            }
+                        }
+                    }
+                    unsigned fr = 0;  // bit kk: u[kk] was not in the visited set
+                    bool forgot = false;
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) {
+                        if (u[kk] >= 0) {
+                            const int ins = visit_set(table, a, (uint32_t)u[kk]);
+                            if (ins != 0) fr |= 1u << kk;
+                            if (ins >= 2) forgot = true;
+                        }
+                    }
+                    if (forgot) ctl.unsafe = 1;  // a vertex may have been forgotten: repeats possible
+                    const int cnt = __popc(fr);
+                    int incl = cnt;  // inclusive scan of the per-lane counts
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int v = __shfl_up_sync(kFull, incl, off);
+                        if (lane >= off) incl += v;
+                    }
+                    int pos = nf + incl - cnt;
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) {
+                        if (fr >> kk & 1u) {
+                            fresh[pos++] = make_uint2((uint32_t)u[kk], urow[kk]);
+                            if (a.l2_prefetch && (urow[kk] < (uint32_t)a.n || a.group_prefetch))
+                                prefetch_row_l2(a.base, row_bytes, urow[kk]);
+                        }
+                    }
+                    nf += __shfl_sync(kFull, incl, 31);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (nf) {
+                    atomicAdd(&ctl.wevals, nf);
+                    if (a.visited_mode == 0) atomicAdd(&ctl.hash_count, nf);
+                }
+            }
+            ANN_PHASE(1)
+
+            // --- distances of this warp's fresh rows; only candidates below the L-th queued entry survive
+            const int L = ctl.L;
+            const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
+            // four chunks in flight per lane (one 128-d BF16 row per 4-lane team in one round trip)
+            if (!gather_fixed<STORE, L2>(a.base, a.scales, cpr, a.team_lanes, qv, nullptr, fresh, nf, 0, 1, limit,
+                                         surv, &ctl.ns[par]))
+                warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, nf, a.team_lanes, limit, surv,
+                                                 &ctl.ns[par]);
+            __syncthreads();
+            ANN_PHASE(2)
+            const int ns = ctl.ns[par];
+            if (lane < my_rows) Q[sel_pos[lane]] |= kChecked;  // the selection is taken: mark it
+            if (tid == 0) {
+                ctl.ns[par ^ 1] = 0;  // next step's counter (last read before this step's barrier)
+                ctl.steps++;
+                ctl.expansions += nact;
+                ctl.first_un = last_pos + 1;
+                ctl.do_reset = a.visited_mode == 0 && ctl.hash_count * 2 > H;
+            }
+            if (ns > 0) {
+                // --- sort the survivors by (key, id) into srt
+                entry_t *srt = surv;
+                if (ns <= 32) {
+                    if (warp == 0) {
+                        entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
+                        e = warp_sort32(e);
+                        surv[lane] = e;
+                    }
+                    __syncthreads();
+                } else if (ns > 64 && ns <= NT) {
+                    // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
+                    block_rank_sort<NT>(surv, ns, cand);  // the fresh lists are not needed any more
+                    srt = cand;
+                } else {
+                    int P = 64;
+                    while (P < ns) P <<= 1;
+                    for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+                    __syncthreads();
+                    block_bitonic_sort<NT>(surv, P);
+                }
+                int ncl = ns;
+                if (ctl.unsafe) {
+                    // --- drop ids already queued or repeated (only after the visited set forgot)
+                    int any = 0;
+                    for (int j = tid; j < ns; j += NT) {
+                        const entry_t c = srt[j];
+                        bool d = (j > 0 && srt[j - 1] == c);
+                        if (!d) {
+                            const int pos = count_below(Q, qlen, c);
+                            d = pos < qlen && (Q[pos] & kMask) == c;
+                        }
+                        dup[j] = d;
+                        any |= d;
+                    }
+                    if (__syncthreads_or(any)) {
+                        if (warp == 0) {
+                            int outp = 0;
+                            for (int b = 0; b < ns; b += 32) {
+                                const int j = b + lane;
+                                const bool keep = j < ns && !dup[j];
+                                const entry_t c = j < ns ? srt[j] : 0ull;
+                                const unsigned bal = __ballot_sync(kFull, keep);
+                                if (keep) srt[outp + __popc(bal & lt_mask)] = c;
+                                outp += __popc(bal);
+                            }
+                            if (lane == 0) ctl.anydup = outp;
+                        }
+                        __syncthreads();
+                        ncl = ctl.anydup;
+                        if (tid == 0) ctl.dropped += ns - ncl;
+                    }
+                }
+                // --- merge queue and survivors, truncated to L (merge path: one search per thread); the first
+                // survivor's rank among the old entries bounds the new queue's checked prefix
+                if (tid == 0 && ncl > 0) {
+                    const int p0 = count_below(Q, qlen, srt[0]);
+                    if (p0 < ctl.first_un) ctl.first_un = p0;
+                }
+                block_merge_path<NT>(Q, qlen, srt, ncl, Qn, ctl.L);
+                __syncthreads();  // the new queue is complete; nothing of the old one is read again
+                qlen = min(ctl.L, qlen + ncl);
+                entry_t *tmp = Q;
+                Q = Qn;
+                Qn = tmp;
+            } else {
+                __syncthreads();  // the marks and first_un are visible before the next select
+            }
+            ANN_PHASE(3)
+            if (step % a.t == 0) Mcur = min(2 * Mcur, ctl.Mmax);
+        }
+#undef ANN_PHASE
+
+        // --- output: first k of the queue, optionally re-ranked with FP32 rows
+        const int k = ctl.k;
+        const entry_t *res = Q;
+        if (a.rerank) {
+            for (int i = tid; i < qlen; i += NT) {
+                const uint32_t id = entry_id(Q[i]);
+                cand[i] = (entry_t)id;
+                if (a.l2_prefetch) prefetch_row_l2(a.base32, (uint32_t)a.d_pad32 * 4u, id);
+            }
+            if (tid == 0) ctl.ns[0] = 0;
+            __syncthreads();
+            // every key is kept (limit = the empty entry), in whatever order the teams finish
+            if (!gather_fixed<ANN_STORE_F32, L2>(a.base32, nullptr, (uint32_t)a.d_pad32 / 4u, a.team_lanes32, qv,
+                                                 cand, nullptr, qlen, warp, NW, kEmptyEntry, surv, &ctl.ns[0]))
+                compute_keys_teams_m<ANN_STORE_F32, NT, L2, 2>(a.base32, nullptr, a.d_pad32, qv, cand, qlen,
+                                                               a.team_lanes32, kEmptyEntry, surv, &ctl.ns[0]);
+            __syncthreads();
+            if (k <= 32) {
+                // only the k best are output: select them instead of sorting the whole queue
+                res = block_topk<NT>(surv, qlen, k, cand, surv);
+            } else {
+                int P = 32;
+                while (P < qlen) P <<= 1;
+                for (int i = qlen + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+                __syncthreads();
+                block_bitonic_sort<NT>(surv, P);
+                res = surv;
+            }
+        }
+        int64_t *oid = a.out_ids + (size_t)qi * a.k;
+        float *odist = a.out_dists + (size_t)qi * a.k;
+        for (int i = tid; i < a.k; i += NT) {
+            if (i < k && i < qlen) {
+                oid[i] = (int64_t)entry_id(res[i]);
+                odist[i] = entry_key(res[i]);
+            } else {
+                oid[i] = -1;
+                odist[i] = __int_as_float(0x7f800000);
+            }
+        }
+        if (tid == 0 && a.stats) {
+            ann_query_stats st;
+            st.steps = ctl.steps;
+            st.expansions = ctl.expansions;
+            st.evals = ctl.evals + ctl.wevals;
+            st.hash_resets = ctl.resets;
+            st.dup_dropped = ctl.dropped;
+            st.merges = 0;
+            st.t_start_ns = ctl.t0;
+            st.t_end_ns = global_ns();
+            a.stats[qi] = st;
+        }
+        if (tid == 0 && prof)
+            for (int i = 0; i < 4; ++i) a.phase_cycles[(size_t)qi * 4 + i] = ctl.ph[i];
+        if (!a.persistent) break;
+        __syncthreads();
+    }
+}
+
+// One kernel per metric: the distance formula is a compile-time choice.
+template <int NT, int STORE>
+static auto sync_kernel_for(int metric) {
+    return metric == ANN_METRIC_L2 ? sync_search_kernel<NT, STORE, true> : sync_search_kernel<NT, STORE, false>;
+}
+
+// Launch / occupancy of the kernels of one storage type (each storage type is
+// instantiated in a translation unit of its own: search_sync_<storage>.cu).
+template <int STORE>
+cudaError_t launch_sync_store(const SearchArgs &a, int threads, int smem, int grid, cudaStream_t s) {
+    auto go = [&](auto fn) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        switch (threads) {
+            case 64: fn<<<grid, 64, smem, s>>>(a); break;
+            case 128: fn<<<grid, 128, smem, s>>>(a); break;
+            case 256: fn<<<grid, 256, smem, s>>>(a); break;
+            case 512: fn<<<grid, 512, smem, s>>>(a); break;
+        }
+        return cudaGetLastError();
+    };
+    switch (threads) {
+        case 64: return go(sync_kernel_for<64, STORE>(a.metric));
+        case 128: return go(sync_kernel_for<128, STORE>(a.metric));
+        case 256: return go(sync_kernel_for<256, STORE>(a.metric));
+        case 512: return go(sync_kernel_for<512, STORE>(a.metric));
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int STORE>
+cudaError_t occupancy_sync_store(int metric, int threads, int smem, int *bps) {
+    auto occ = [&](auto fn, int nt) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, nt, smem);
+    };
+    switch (threads) {
+        case 64: return occ(sync_kernel_for<64, STORE>(metric), 64);
+        case 128: return occ(sync_kernel_for<128, STORE>(metric), 128);
+        case 256: return occ(sync_kernel_for<256, STORE>(metric), 256);
+        case 512: return occ(sync_kernel_for<512, STORE>(metric), 512);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ann

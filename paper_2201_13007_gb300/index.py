@@ -50,6 +50,11 @@ class Index:
         i = _abi.ann_index_get_info(self.handle)
         return {f: getattr(i, f) for f, _ in _abi.IndexInfo._fields_}
 
+    def group_neighbors(self, hot_fraction, prefetch="block"):
+        """Neighbour groups for the hottest vertices by in-degree
+        (ann_index_group_neighbors); prefetch "block" or "rows"."""
+        _abi.ann_index_group_neighbors(self.handle, hot_fraction, {"block": 0, "rows": 1}[prefetch])
+
     def close(self):
         if getattr(self, "_h", None):
             _abi.ann_index_destroy(self.handle)

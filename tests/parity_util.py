@@ -83,7 +83,7 @@ def compare_float(gpu_ids, gpu_keys, orc_ids, orc_keys, tie_events, base, q, met
                              for r in exempt]))
     rep = {"rows": int(gpu_ids.shape[0]), "tie_free": int(clean.sum()), "tie_rows": int((~clean).sum()),
            "tie_rows_within_swap_rule": int((~clean & good_rows).sum()), "exempt_rows": exempt.tolist(),
-           "exempt_recall": rec, "match_frac": float(good_rows.mean())}
+           "exempt_recall": rec, "match_frac": float(good_rows.mean()) if good_rows.size else 1.0}
     print(f"compare_float{(' ' + label) if label else ''}: {rep}")
     assert exempt.size <= max_exempt_frac * gpu_ids.shape[0], f"{exempt.size} exempt rows: {exempt.tolist()}"
     assert rec >= min_tie_recall, f"recall vs oracle on the exempt rows {rec}"

@@ -234,6 +234,10 @@ def test_reduced_precision_with_rerank(ann, oracle_mod, storage):
     r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, o_ids, 10)
     compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
                   np.zeros(clean.sum()), w.base, w.queries[clean], "l2")
+    # and on every row, the re-rank of the GPU's own final queue
+    r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, ids_nr.cpu().numpy(), 10)
+    compare_float(ids_rr.cpu().numpy(), d_rr.cpu().numpy(), r_ids, r_keys, np.zeros(r_ids.shape[0]), w.base,
+                  w.queries, "l2", max_exempt_frac=0.0)
     ix.close()
 
 
@@ -259,24 +263,28 @@ def test_high_dimension_d960_with_rerank(ann, oracle_mod, storage):
                                             tie_tol=fp32_tie_window(stored, w.queries, "l2")[0])
     compare_float(ids_nr.cpu().numpy(), d_nr.cpu().numpy(), o_ids, o_keys, o_st["tie_events"], stored,
                   w.queries, "l2", label=f"d=960 {storage} stored keys")
-    clean = o_st["tie_events"] == 0
-    r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, o_ids, 10)
-    compare_float(ids_rr.cpu().numpy()[clean], d_rr.cpu().numpy()[clean], r_ids[clean], r_keys[clean],
-                  np.zeros(clean.sum()), w.base, w.queries[clean], "l2", label=f"d=960 {storage} re-rank")
+    # the re-rank step itself, on every row: the oracle re-ranks the GPU's own final queue (the same
+    # deterministic search without re-rank) with the FP32 rows
+    r_ids, r_keys = oracle_mod.rerank(w.base, w.queries, ids_nr.cpu().numpy(), 10)
+    compare_float(ids_rr.cpu().numpy(), d_rr.cpu().numpy(), r_ids, r_keys, np.zeros(r_ids.shape[0]), w.base,
+                  w.queries, "l2", max_exempt_frac=0.0, label=f"d=960 {storage} re-rank")
     ix.close()
 
 
-@pytest.mark.parametrize("visited_mode,slot_bytes", [(2, 1), (3, 4)])
+@pytest.mark.parametrize("visited_mode,slot_bytes", [(2, 1), (3, 4), (4, 4)])
 @pytest.mark.parametrize("hash_bits", [8, 10, 12])
 def test_direct_mapped_visited_cache_keeps_ids(ann, oracle_mod, sift_small, hash_bits, visited_mode, slot_bytes):
     """The direct-mapped visited cache forgets a vertex whenever another one
-    hashes to its slot; ids and keys must still be exact (reading 14). Mode 2
-    keeps a one-byte tag per slot here (20,000 ids need 15 bits), mode 3 a
-    full id."""
+    hashes to its slot, the set-associative one when a fourth vertex enters a
+    full set; ids and keys must still be exact (reading 14). Mode 2 keeps a
+    one-byte tag per slot here (20,000 ids need 15 bits), mode 3 a full id,
+    mode 4 three tags per set word."""
     _, Index, stats_dict = ann
     w = sift_small
     ix = Index(w.base, w.adj, w.entry)
     assert ix.describe(64, 10, 128, 8, hash_bits=hash_bits, visited_mode=visited_mode)["visited_slot_bytes"] == slot_bytes
+    if visited_mode == 4:
+        assert ix.describe(64, 10, 128, 8, hash_bits=hash_bits, visited_mode=4)["visited_ways"] == 3
     ix.close()
     ids, dists, st = _run(Index, w, L=128, M=8, hash_bits=hash_bits, visited_mode=visited_mode)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=128, K=10,
