@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-single", action="store_true")
-    ap.add_argument("--workload", default="sift", choices=["sift", "gist", "deep-batch", "serve"],
+    ap.add_argument("--workload", default="sift", choices=["sift", "gist", "deep-batch", "serve", "adaptive"],
                     help="sift: the headline (default); the others measure the precision, batching and serving "
                          "workloads and print one JSON line each")
     ap.add_argument("--no-legs", action="store_true",
@@ -368,6 +368,23 @@ def run_ours(args):
             grouping = {"error": repr(e)}
             log("grouping leg failed:", e)
 
+    # ---- the graph the search runs on (input preparation, not the method): degree, reachability and how many
+    # of a vertex's exact 32 nearest neighbours are its out-neighbours (exact 32-NN of 2,000 sampled vertices)
+    gq = {}
+    if not args.no_legs:
+        try:
+            src = np.random.Generator(np.random.PCG64(9)).choice(w.n, size=2000, replace=False)
+            nn = exact_topk_gpu(w.base, w.base[src], 33, torch)
+            knn = np.full((w.n, 32), -1, np.int64)
+            for j, v in enumerate(src):
+                knn[v] = [u for u in nn[j] if u != v][:32]
+            gq = synth.graph_quality(w.adj, w.entry, sample=2000)
+            cov = [len(set(knn[v].tolist()) & set(w.adj[v][w.adj[v] >= 0].tolist())) / 32 for v in src]
+            gq["exact_32nn_in_out_edges"] = float(np.mean(cov))
+        except Exception as e:
+            gq = {"error": repr(e)}
+        torch.cuda.empty_cache()
+
     # ---- plain one query per launch (latency form) on a subset
     single = {}
     for tgt in TARGETS:
@@ -470,6 +487,7 @@ def run_ours(args):
         "one_query_per_launch": {str(k): v for k, v in single.items()},
         "async_alg3_bf16_rerank": async_pts,
         "neighbour_grouping": grouping,
+        "graph_quality": gq,
         "setup_s": setup_s,
     }
     # the precision (1M x 960) and batching (100,000 uneven queries) workloads, short, as extra keys
@@ -809,6 +827,54 @@ def run_gist(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------- adaptive-sync refinements
+
+def run_adaptive(args):
+    """Merge triggers of the asynchronous walkers (Algorithm 3) compared at
+    equal recall on the 1M x 128 workload: Algorithm 2 (mean update position
+    >= L * R) over a sweep of R, and the stall count (mean number of a
+    walker's expansions since the deal that inserted nothing into its top L)
+    over a sweep of the patience P. For each trigger and recall target, the
+    cheapest (L, M) in a sweep, with distance evaluations and merges per
+    query and QPS (BF16 storage + FP32 re-rank, persistent grid)."""
+    import torch
+    from paper_2201_13007_gb300 import synth
+    from paper_2201_13007_gb300.index import Index
+    w = synth.make_workload("sift", args.n, args.nq)
+    gt = exact_topk_gpu(w.base, w.queries, K, torch)
+    torch.cuda.empty_cache()
+    ix = Index(w.base, w.adj, w.entry, storage="bf16", keep_f32=True)
+    q = torch.from_numpy(w.queries).cuda()
+    nq = q.shape[0]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    triggers = [("alg2", {"R_ratio": R}) for R in (0.6, 0.7, 0.8, 0.9, 1.0)]
+    triggers += [("stall", {"patience": P}) for P in (1.0, 2.0, 4.0)]
+    Ls = (64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024)
+    out = {"workload": f"sift-like {args.n} x 128, {nq} queries, k=10, async walkers, BF16 + FP32 re-rank",
+           "targets": {}}
+    for name, tkw in triggers:
+        label = f"{name}({list(tkw.values())[0]})"
+        rows = []
+        for M in (4, 8):
+            for L in Ls:
+                kw = dict(mode="async", rerank=True, persistent=True, **tkw)
+                st = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
+                ids, _ = ix.search(q, K, L, M, stats=st, **kw)
+                t = float(np.mean(event_time(torch, lambda: ix.search(q, K, L, M, **kw), 2, 1, flush)))
+                sn = st.cpu().numpy()
+                rec = recall_at_k(ids.cpu().numpy(), gt)
+                rows.append({"L": L, "M": M, "recall": rec, "qps": nq / t, "evals": float(sn[:, 2].mean()),
+                             "merges": float(sn[:, 5].mean()), "steps": float(sn[:, 0].mean())})
+                if rec >= 0.993:
+                    break
+        for tgt in (0.95, 0.99):
+            ok = [r for r in rows if r["recall"] >= tgt]
+            if ok:
+                out["targets"].setdefault(str(tgt), {})[label] = max(ok, key=lambda r: r["qps"])
+        log(label, "done")
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------- batching
 
 def run_deep_batch(args):
@@ -978,6 +1044,8 @@ def main():
         run_deep_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "adaptive":
+        run_adaptive(args)
     else:
         run_ours(args)
 

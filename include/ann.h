@@ -144,8 +144,9 @@ typedef struct {
      * holding the tags (the same split of the hashed id) of the 3 (or, for
      * ids too long for three, 2) vertices that entered the set last; a
      * fourth evicts the oldest. 2 and 3 are for the one-CTA sync kernel
-     * only, 4 for the one-CTA sync and async kernels. 0 = auto (one-CTA sync
-     * kernel: 4 when L >= 128, else 3; async walkers: 4; clusters: 1). No
+     * only; clusters take 4 (each CTA holds the vertices it owns). 0 = auto
+     * (one-CTA sync kernel: 4 when L >= 128, else 3; async walkers and
+     * clusters: 4). No
      * form ever reports a vertex it did not see; they only forget. In sync
      * mode that changes the number of distance evaluations but never the
      * results; asynchronous walkers may also queue and expand a forgotten
@@ -168,6 +169,21 @@ typedef struct {
      * can differ in the last bits between settings; integer-valued data
      * gives identical keys. */
     int32_t team_lanes;
+    /* Async mode: the merge test of the walkers. 0 = Algorithm 2 (mean
+     * update position >= L * R_ratio). 1 = stall count: each walker counts
+     * its expansions since the deal that put no new candidate into the first
+     * L entries of its private queue, and the checker merges when the mean
+     * count over the walkers that received a non-empty deal reaches
+     * `patience` (INFINITY = never early). Sec. 4.3 leaves the metric open;
+     * this one measures the wasted expansions directly. */
+    int32_t merge_rule;
+    float patience;
+    /* One-CTA sync kernel, distance gather: 1 = each warp gathers the rows of
+     * the vertices it found fresh (no barrier between expand and distance);
+     * 2 = the CTA's fresh vertices go into one list that all warps gather
+     * (one barrier more, balanced when rows are long and few per warp); 0 =
+     * auto (2). Results never depend on it. */
+    int32_t gather;
 } ann_search_params;
 
 /* Build an index (Sec. 2.1: "preprocess P").

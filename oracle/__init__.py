@@ -61,6 +61,7 @@ class Graph(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("K", ctypes.c_int32), ("M0", ctypes.c_int32),
                 ("M_max", ctypes.c_int32), ("t", ctypes.c_int32), ("R_ratio", ctypes.c_double),
+                ("merge_rule", ctypes.c_int32), ("patience", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("tie_tol", ctypes.c_double),
                 ("tie_abs", ctypes.c_double)]
 
@@ -122,10 +123,13 @@ def _graph(base, adj, entry, metric):
     return g, (base, adj)
 
 
-def _params(L, K, M0=1, M_max=1, t=1, R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0):
+def _params(L, K, M0=1, M_max=1, t=1, R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0,
+            patience=None):
+    """patience=None: Algorithm 2's merge test (R_ratio); a number: the stall-count test."""
     return Params(L=int(L), K=int(K), M0=int(M0), M_max=int(M_max), t=int(t),
-                  R_ratio=float(R_ratio), max_steps=int(max_steps), tie_tol=float(tie_tol),
-                  tie_abs=float(tie_abs))
+                  R_ratio=float(R_ratio), merge_rule=0 if patience is None else 1,
+                  patience=0.0 if patience is None else float(patience), max_steps=int(max_steps),
+                  tie_tol=float(tie_tol), tie_abs=float(tie_abs))
 
 
 def _check(rc, what):
@@ -134,9 +138,11 @@ def _check(rc, what):
 
 
 def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M_max=1, t=1,
-           R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0, nthreads=1):
+           R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0, nthreads=1, patience=None):
     """Run one of the paper's searches for every query. Returns (ids int64
-    nq x K, keys float64 nq x K, stats structured array nq)."""
+    nq x K, keys float64 nq x K, stats structured array nq). For "speedann",
+    patience=None merges by Algorithm 2 (R_ratio); a number merges by the
+    stall count against that patience."""
     g, keep = _graph(base, adj, entry, metric)
     q = _f32(queries)
     if q.ndim == 1:
@@ -145,7 +151,7 @@ def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M
     ids = np.empty((nq, K), np.int64)
     keys = np.empty((nq, K), np.float64)
     st = np.zeros(nq, _STATS_DTYPE)
-    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs)
+    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs, patience)
     rc = lib().orc_search(ALGOS[algo], ctypes.byref(g), ctypes.byref(p), _ptr(q), nq,
                           _ptr(ids), _ptr(keys), _ptr(st), int(nthreads))
     _check(rc, "search")
@@ -154,7 +160,7 @@ def search(base, adj, entry, queries, *, algo="topm", metric="l2", L, K, M0=1, M
 
 
 def search_trace(base, adj, entry, query, *, algo="topm", metric="l2", L, K, M0=1, M_max=1, t=1,
-                 R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0):
+                 R_ratio=float("inf"), max_steps=-1, tie_tol=1e-5, tie_abs=0.0, patience=None):
     """One query with its full final state: dict with ids, keys, stats, the
     final queue (ids, keys, checked), the visited set in visit order and the
     expansion order."""
@@ -173,7 +179,7 @@ def search_trace(base, adj, entry, query, *, algo="topm", metric="l2", L, K, M0=
     ids = np.empty(K, np.int64)
     keys = np.empty(K, np.float64)
     st = Stats()
-    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs)
+    p = _params(L, K, M0, M_max, t, R_ratio, max_steps, tie_tol, tie_abs, patience)
     rc = lib().orc_search_trace(ALGOS[algo], ctypes.byref(g), ctypes.byref(p), _ptr(q), _ptr(ids),
                                 _ptr(keys), ctypes.byref(st), ctypes.byref(tr))
     _check(rc, "search_trace")

@@ -23,7 +23,11 @@
  *                   at M0 and doubles every t steps up to M_max.
  *   ALGO_SPEEDANN   Algorithm 3 with Algorithm 2 (CheckMetrics, the
  *                   update-position test mean(U) >= L*R) as a deterministic
- *                   lock-step simulation of the walkers (Sec. 4.3).
+ *                   lock-step simulation of the walkers (Sec. 4.3); or, as
+ *                   the merge test, the stall count (mean number of a
+ *                   walker's expansions since the deal that inserted nothing
+ *                   into its top L, against a patience P), one of the other
+ *                   metrics Sec. 4.3 leaves open.
  *   orc_round_*     Storage formats for the reduced-precision variant:
  *                   IEEE binary16, bfloat16 (8-bit significand) and OCP FP8
  *                   E4M3 with a per-vector scale max|x|/448, each written from
@@ -75,6 +79,8 @@ typedef struct {
     int32_t L, K;
     int32_t M0, M_max, t;
     double R_ratio;    /* Alg. 2 position ratio; INFINITY = never merge early */
+    int32_t merge_rule; /* 0 = Alg. 2 (mean update position >= L*R); 1 = stall count (below) */
+    double patience;    /* rule 1: merge when the mean stall count reaches this; INFINITY = never */
     int64_t max_steps; /* stop after this many steps; < 0 = run to convergence */
     double tie_tol;    /* relative gap under which a boundary decision is logged */
     double tie_abs;    /* plus this absolute gap (inner-product keys can be near zero) */
@@ -365,6 +371,23 @@ static int check_metrics(const int32_t *U, const uint8_t *active, int32_t M, int
     return sum / (double)cnt >= (double)L * Rr;
 }
 
+/* The stall-count merge test (an alternative to CheckMetrics; Sec. 4.3 leaves
+ * the choice of metric open): stall[w] counts the expansions walker w made
+ * since the deal that put no new candidate into the first L entries of its
+ * private queue (update position L). True when the mean over the walkers that
+ * received a non-empty deal reaches the patience P. */
+static int check_stall(const int32_t *stall, const uint8_t *active, int32_t M, double P) {
+    double sum = 0.0;
+    int32_t cnt = 0;
+    for (int32_t w = 0; w < M; ++w)
+        if (active[w]) {
+            sum += (double)stall[w];
+            cnt++;
+        }
+    if (cnt == 0) return 0;
+    return sum / (double)cnt >= P;
+}
+
 /* Deterministic simulation of Algorithm 3: a global queue S and T private
  * queues. Each global step deals S's unchecked entries to the M walkers;
  * walkers then advance in lock-step sub-steps, in walker order, each running
@@ -380,12 +403,13 @@ static int run_speedann(const orc_graph *g, const orc_params *p, const float *q,
     entry_t *LS = (entry_t *)malloc(sizeof(entry_t) * (size_t)cap * (size_t)T);
     int32_t *lsn = (int32_t *)calloc((size_t)T, sizeof(int32_t));
     int32_t *U = (int32_t *)calloc((size_t)T, sizeof(int32_t));
+    int32_t *stall = (int32_t *)calloc((size_t)T, sizeof(int32_t));
     uint8_t *active = (uint8_t *)calloc((size_t)T, 1);
     entry_t *pool = (entry_t *)malloc(sizeof(entry_t) * ((size_t)L + (size_t)cap * (size_t)T));
     int32_t *act_list = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
     int64_t *new_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
-    if (!S || !LS || !lsn || !U || !active || !pool || !act_list || !new_ids) {
-        free(S); free(LS); free(lsn); free(U); free(active); free(pool); free(act_list); free(new_ids);
+    if (!S || !LS || !lsn || !U || !stall || !active || !pool || !act_list || !new_ids) {
+        free(S); free(LS); free(lsn); free(U); free(stall); free(active); free(pool); free(act_list); free(new_ids);
         return ORC_ERR_OOM;
     }
     int32_t len = 0;
@@ -397,7 +421,7 @@ static int run_speedann(const orc_graph *g, const orc_params *p, const float *q,
     int rc = ORC_OK;
     while (p->max_steps < 0 || st->steps < p->max_steps) {
         /* deal: unchecked entries of S go round-robin, by rank, to the M walkers */
-        for (int32_t w = 0; w < M; ++w) { lsn[w] = 0; U[w] = 0; active[w] = 0; }
+        for (int32_t w = 0; w < M; ++w) { lsn[w] = 0; U[w] = 0; stall[w] = 0; active[w] = 0; }
         int32_t kept = 0, dealt = 0;
         for (int32_t i = 0; i < len; ++i) {
             if (S[i].checked) {
@@ -446,10 +470,13 @@ static int run_speedann(const orc_graph *g, const orc_params *p, const float *q,
                     for (int32_t k = 0; k < n_new; ++k)
                         if (Q[j].id == new_ids[k]) { upos = j; break; }
                 U[w] = upos;
+                if (upos == L) stall[w]++;
             }
             if (!any) break;
             st->substeps++;
-            if (checker_expanded && check_metrics(U, active, M, L, p->R_ratio)) {
+            const int test = p->merge_rule == 1 ? check_stall(stall, active, M, p->patience)
+                                                : check_metrics(U, active, M, L, p->R_ratio);
+            if (checker_expanded && test) {
                 do_merge = 1;
                 checker++;
             }
@@ -477,7 +504,7 @@ static int run_speedann(const orc_graph *g, const orc_params *p, const float *q,
     }
     write_outputs(S, len, p, ids, keys, st, tr, vs);
 done:
-    free(S); free(LS); free(lsn); free(U); free(active); free(pool); free(act_list); free(new_ids);
+    free(S); free(LS); free(lsn); free(U); free(stall); free(active); free(pool); free(act_list); free(new_ids);
     return rc;
 }
 
@@ -498,6 +525,8 @@ static int check_params(int32_t algo, const orc_params *p) {
         if (p->M0 < 1 || p->M_max < 1 || p->t < 1) return ORC_ERR_ARG;
     }
     if (algo == ALGO_SPEEDANN && !(p->R_ratio >= 0.0)) return ORC_ERR_ARG;
+    if (algo == ALGO_SPEEDANN && (p->merge_rule < 0 || p->merge_rule > 1 || !(p->patience >= 0.0)))
+        return ORC_ERR_ARG;
     if (algo < ALGO_BFIS || algo > ALGO_SPEEDANN) return ORC_ERR_ARG;
     return ORC_OK;
 }

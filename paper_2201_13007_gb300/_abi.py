@@ -52,7 +52,8 @@ class SearchParams(ctypes.Structure):
                 ("M_per_query", ctypes.c_void_p), ("stats", ctypes.c_void_p),
                 ("order", ctypes.c_void_p), ("cluster", ctypes.c_int32), ("phase_cycles", ctypes.c_void_p),
                 ("visited_mode", ctypes.c_int32), ("l2_prefetch", ctypes.c_int32),
-                ("team_lanes", ctypes.c_int32)]
+                ("team_lanes", ctypes.c_int32), ("merge_rule", ctypes.c_int32), ("patience", ctypes.c_float),
+                ("gather", ctypes.c_int32)]
 
 
 class BucketConfig(ctypes.Structure):

@@ -194,6 +194,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (M0 < 1 || t < 1) return fail(ANN_ERR_ARG, "M0=%d and t=%d must be >= 1", M0, t);
     if (p->rerank && !x.base32) return fail(ANN_ERR_ARG, "rerank needs an FP32 copy (ANN_INDEX_KEEP_F32)");
     if (async && !(p->R_ratio >= 0.f)) return fail(ANN_ERR_ARG, "R_ratio must be >= 0 (or INFINITY)");
+    if (p->merge_rule != 0 && p->merge_rule != 1) return fail(ANN_ERR_ARG, "merge_rule=%d not in {0, 1}", p->merge_rule);
+    if (p->merge_rule == 1 && !(p->patience >= 0.f))
+        return fail(ANN_ERR_ARG, "patience must be >= 0 (or INFINITY) with merge_rule 1");
     if (async && M > 32) return fail(ANN_ERR_ARG, "async mode runs one warp per walker: M=%d > 32", M);
     const int csize = p->cluster > 1 ? p->cluster : 1;
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8)
@@ -227,8 +230,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
         return fail(ANN_ERR_ARG, "visited_mode=%d not in {0, 1, 2, 3, 4}", p->visited_mode);
     if ((p->visited_mode == 2 || p->visited_mode == 3) && (async || csize > 1))
         return fail(ANN_ERR_ARG, "the direct-mapped visited caches 2 and 3 are for the one-CTA sync kernel");
-    if (p->visited_mode == 4 && csize > 1)
-        return fail(ANN_ERR_ARG, "the set-associative visited cache is for the one-CTA kernels");
+    if (csize > 1 && p->visited_mode != 0 && p->visited_mode != 4)
+        return fail(ANN_ERR_ARG, "clusters keep their visited sets in the set-associative cache (visited_mode 0 or 4)");
     int idbits = 1;  // bits of the largest vertex id
     while (idbits < 31 && (int64_t(1) << idbits) < x.n) ++idbits;
     // tags per set word of the set-associative cache with 2^bits sets (0 if not even two fit)
@@ -242,9 +245,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     // its exchange is cheaper than a CAS)
     // (the asynchronous walkers take it at every L: a set that forgets lets a walker queue, expand and
     // count again what another walker already saw, which changes when Algorithm 2 merges)
-    int vmode = p->visited_mode == 0 ? (csize > 1 ? 1 : (async || L >= 128) ? 4 : 3) : p->visited_mode;
+    int vmode = p->visited_mode == 0 ? ((csize > 1 || async || L >= 128) ? 4 : 3) : p->visited_mode;
     if (vmode == 4 && ways_for(15) < 2) {
-        if (p->visited_mode == 4)
+        if (p->visited_mode == 4 || csize > 1)
             return fail(ANN_ERR_ARG, "visited_mode=4: ids of %d bits leave no room for two tags per set word", idbits);
         vmode = async ? 1 : 2;
     }
@@ -299,6 +302,8 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.M0 = M0;
     a.t = t;
     a.R_ratio = p->R_ratio;
+    a.merge_rule = p->merge_rule;
+    a.patience = p->patience;
     a.rerank = p->rerank ? 1 : 0;
     a.hash_bits = hb;
     a.visited_mode = vmode >= 2 ? 1 : 0;
@@ -308,6 +313,10 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     // neighbour groups serve the one-CTA sync kernel (the other kernels read every row by its id)
     a.hot_slot = (!async && csize == 1 && x.n_hot > 0) ? x.hot_slot : nullptr;
     a.group_prefetch = x.group_prefetch;
+    if (p->gather < 0 || p->gather > 2) return fail(ANN_ERR_ARG, "gather=%d not in {0, 1, 2}", p->gather);
+    // auto: one list per CTA (measured equal or faster than per-warp lists on every workload: much faster for
+    // long rows, where a warp has few rows per step and its passes run part-empty; within 1 % for 128-d rows)
+    a.block_gather = p->gather != 1;
     {
         const int tl = p->team_lanes;
         if (!(tl == -1 || tl == 0 || (tl > 0 && tl <= 32 && (tl & (tl - 1)) == 0)))
@@ -337,9 +346,9 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     a.Lcap = L;
     int need = M * x.R;
     if (a.rerank && L > need) need = L;
-    if (!async && csize == 1) {  // the warps' fresh lists live in the candidate segment
+    if (!async) {  // the warps' fresh lists live in the candidate segment
         const int nw = threads / 32;
-        const int fresh_entries = nw * ((M + nw - 1) / nw) * x.R;  // one (id, row) pair per entry
+        const int fresh_entries = nw * ((M * x.R + nw - 1) / nw);  // one (id, row) pair per entry
         if (fresh_entries > need) need = fresh_entries;
     }
     a.Ccap = ann::next_pow2(need < 32 ? 32 : need);

@@ -54,10 +54,10 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Shared memory of the one-CTA sync kernel with nw warps. The cand segment
-// holds each warp's fresh (id, row) pairs during a step (nw * ceil(Mcap /
-// nw) * R of them, one per 8-byte entry; the host makes Ccap at least that)
-// and sort output after it;
-// act holds each warp's selected vertices and their queue positions.
+// holds each warp's fresh (id, row) pairs during a step (nw * ceil(Mcap * R /
+// nw) of them, one per 8-byte entry; the host makes Ccap at least that) and
+// sort output after it; act holds the step's selected vertices and their
+// queue positions.
 __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
                                                   int slot_bytes, int nw) {
     SmemLayout s;
@@ -69,7 +69,7 @@ __host__ __device__ inline SmemLayout sync_layout(int qfloats, int Lcap, int Cca
     s.cand2_off = o; o += align16(Ccap * 8);
     s.dup_off = o;  o += align16(Ccap);
     s.hash_off = o; o += align16((1 << hash_bits) * slot_bytes);
-    s.act_off = o;  o += align16(2 * nw * ((Mcap + nw - 1) / nw) * 4);
+    s.act_off = o;  o += align16(2 * Mcap * 4);
     s.total = o;
     return s;
 }
@@ -90,6 +90,8 @@ struct SearchArgs {
     const int32_t *k_arr, *L_arr, *M_arr;
     int32_t M0, t;
     float R_ratio;
+    int32_t merge_rule;    // async: 0 = Algorithm 2; 1 = stall count against `patience`
+    float patience;
     int32_t rerank;
     int32_t hash_bits;
     int32_t visited_mode;  // 0 = open addressing, reset when half full; 1 = direct-mapped, forgets on collision
@@ -99,6 +101,7 @@ struct SearchArgs {
     int32_t l2_prefetch;   // 1 = L2 prefetch of each candidate row once it passes the visited filter
     const int32_t *hot_slot; // neighbour groups: n entries, the group of a hot vertex or -1 (nullptr: none)
     int32_t group_prefetch;  // 0 = one bulk prefetch per hot vertex's block; 1 = the fresh rows only
+    int32_t block_gather;    // one-CTA sync kernel: 1 = the CTA's fresh rows in one list gathered by all warps
     int32_t team_lanes;    // distance gather: log2 of the lanes that share one candidate row
     int32_t team_lanes32;  // the same for the FP32 rows of the re-rank
     int64_t *out_ids;

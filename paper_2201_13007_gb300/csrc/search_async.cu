@@ -13,9 +13,11 @@
 //          synchronised visiting map of Sec. 4.4), and records its update
 //          position (best rank at which a new candidate landed, L if none).
 //          A CTA barrier ends the sub-step; then every thread evaluates the
-//          same Algorithm 2 test for the checker walker (round robin): if the
-//          checker expanded in this sub-step and mean(U) >= L * R, or if no
-//          walker expanded, the walk ends. Sub-steps are cheap on a GPU (one
+//          same merge test for the checker walker (round robin): if the
+//          checker expanded in this sub-step and mean(U) >= L * R (Algorithm
+//          2), or, with the stall rule, the walkers' mean count of expansions
+//          since the deal that inserted nothing into their top L reaches the
+//          patience; or if no walker expanded, the walk ends. Sub-steps are cheap on a GPU (one
 //          CTA barrier), so the walkers advance in lock-step as in the
 //          oracle's reading of Algorithm 3, and every update position the
 //          checker averages is from the same sub-step;
@@ -34,7 +36,8 @@ struct AsyncCtrl {
     int chunk_tot[64];
     int merged_len;
     int hash_count;
-    int walk[2][32];  // per sub-step parity and walker: (update position << 1) | expanded-in-this-sub-step
+    // per sub-step parity and walker: (stall count << 16) | (update position << 1) | expanded-in-this-sub-step
+    int walk[2][32];
 };
 
 __host__ __device__ inline int async_smem_bytes(int qfloats, int Lcap, int walkers, int hash_bits, int *offs) {
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
                 entry_t *Q = LSall + (size_t)warp * Lcap;
                 entry_t *cw = CWall + warp * 32;
                 int ql = warp < nactive ? lsn[warp] : 0;
-                int upos_w = 0;  // this walker's update position (U is reset to 0 at each deal)
+                int upos_w = 0;   // this walker's update position (U is reset to 0 at each deal)
+                int stall_w = 0;  // its expansions since the deal that inserted nothing into its top L
                 for (int sub = 0;; ++sub) {
                     const int par = sub & 1;
                     bool expanded = false;
@@ -258,20 +262,25 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 65536 / (NT * 128))) asyn
                                 if (nk > 0 && p0 < upos) upos = p0;
                             }
                             upos_w = upos;
+                            if (upos == L) stall_w++;
                         }
                     }
-                    if (lane == 0 && warp < T) ctl.walk[par][warp] = (upos_w << 1) | (expanded ? 1 : 0);
+                    if (lane == 0 && warp < T)
+                        ctl.walk[par][warp] = (min(stall_w, 32767) << 16) | (upos_w << 1) | (expanded ? 1 : 0);
                     __syncthreads();  // the sub-step is over: every walker's word for it is written
                     // every thread evaluates the same test (Algorithm 2 for the checker; none expanded = all idle)
                     bool any = false;
-                    int sum = 0;
+                    int sum = 0, stalls = 0;
                     for (int w2 = 0; w2 < nactive; ++w2) {
                         const int wd = ctl.walk[par][w2];
                         any |= (wd & 1) != 0;
-                        sum += wd >> 1;
+                        sum += (wd >> 1) & 0x7FFF;
+                        stalls += wd >> 16;
                     }
                     if (!any) break;
-                    if ((ctl.walk[par][chk] & 1) && (float)sum / (float)nactive >= threshold) {
+                    const bool test = a.merge_rule == 1 ? (float)stalls / (float)nactive >= a.patience
+                                                        : (float)sum / (float)nactive >= threshold;
+                    if ((ctl.walk[par][chk] & 1) && test) {
                         raised = true;
                         break;
                     }

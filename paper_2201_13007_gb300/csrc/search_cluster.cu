@@ -1,19 +1,21 @@
-// search_cluster.cu -- the synchronous top-M search of search_sync.cu with one
-// query spread over a thread-block cluster of C CTAs (C = 2, 4 or 8).
+// search_cluster.cu -- the synchronous top-M search of search_sync.cuh with one
+// query spread over a thread-block cluster of C CTAs (C = 2, 4 or 8): the
+// latency form, for few queries at a time.
 //
 // Every CTA of the cluster keeps an identical copy of the sorted queue and
 // makes the same selection each step (top-M unchecked, Sec. 4.1-4.2). The
-// neighbours of the selected vertices are partitioned by owner: vertex u
-// belongs to CTA (u mod C), which alone keeps it in its visited table and
-// gathers its row, so a step's row gathers are spread over C SMs. Each CTA
-// filters its new candidates by the current L-th entry and publishes them in
-// shared memory (double-buffered by step parity); after one cluster barrier
-// every CTA reads all published lists through distributed shared memory,
-// sorts their union, drops ids already queued and merges - the same inputs
+// step's adjacency slots are split over each CTA's warps as in the one-CTA
+// kernel, but vertex u belongs to CTA (u mod C): only its owner inserts it
+// into its visited set and gathers its row, so a step's row gathers are
+// spread over C SMs. Each CTA filters its new candidates by the current L-th
+// entry and publishes them in shared memory (double-buffered by step parity);
+// after one cluster barrier every CTA reads all published lists through
+// distributed shared memory, sorts their union, drops ids already queued
+// (when some owner's visited set forgot a vertex) and merges: the same inputs
 // in every CTA, so the queues stay identical and every CTA takes the same
 // number of steps and barriers. Because ownership partitions the vertices,
-// the union of the CTAs' new candidates is exactly the single-CTA kernel's,
-// and the results are identical to it.
+// the union of the CTAs' new candidates is exactly the one-CTA kernel's, and
+// the results are identical to it.
 #include <cooperative_groups.h>
 
 #include "search_common.cuh"
@@ -23,37 +25,45 @@ namespace cg = cooperative_groups;
 namespace ann {
 
 struct ClusterCtrl {
-    int nact, ncand, qlen, hash_count, anydup, ns, nloc;
-    int pub_n[2];       // published survivors per step parity
-    int pub_fresh[2];   // new candidates per step parity (for the counters)
-    long long steps, expansions, evals, resets, dropped, t0;
+    int pub_n[2];      // survivors published in the step of this parity
+    int pub_fresh[2];  // fresh vertices of this CTA in the step of this parity
+    int pub_unsafe[2]; // this CTA's visited set may have forgotten a vertex (as of this step)
+    int unsafe, anydup, first_un, sel_found, sel_last, wevals;
+    int rr_n;          // re-rank keys appended (rank 0, after the search; never read by another CTA)
+    long long steps, expansions, dropped, t0;
 };
 
+// Segments: query, two queue buffers, per-warp fresh lists (then sort
+// scratch), published survivors (two parities), the gathered union, dedupe
+// flags, the visited set (this CTA's vertices) and the selection.
 __host__ __device__ inline int cluster_smem_bytes(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap,
                                                   int *off) {
     int o = 0;
     off[0] = o; o += align16(qfloats * 4);          // query
     off[1] = o; o += align16(Lcap * 8);             // queue
     off[2] = o; o += align16(Lcap * 8);             // next queue
-    off[3] = o; o += align16(Ccap * 8);             // local candidates
+    off[3] = o; o += align16(Ccap * 8);             // fresh (id, row) pairs; sort scratch; re-rank ids
     off[4] = o; o += align16(Ccap * 8);             // published survivors, parity 0
     off[5] = o; o += align16(Ccap * 8);             // published survivors, parity 1
-    off[6] = o; o += align16(Ccap * 8);             // gathered union
+    off[6] = o; o += align16(Ccap * 8);             // gathered union; re-rank keys
     off[7] = o; o += align16(Ccap);                 // dup flags
-    off[8] = o; o += align16((1 << hash_bits) * 4); // visited table (own vertices)
-    off[9] = o; o += align16(Mcap * 4);             // selected vertices
+    off[8] = o; o += align16((1 << hash_bits) * 4); // visited set (own vertices)
+    off[9] = o; o += align16(2 * Mcap * 4);         // selected vertices and their queue positions
     return o;
 }
 
-template <int NT, int STORE>
+template <int NT, int STORE, bool L2>
 __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs a) {
+    constexpr int NW = NT / 32;
+    constexpr uint32_t ES = STORE == ANN_STORE_F32 ? 4u : STORE == ANN_STORE_E4M3 ? 1u : 2u;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ClusterCtrl ctl;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t row_bytes = (uint32_t)a.d_pad * (STORE == ANN_STORE_F32 ? 4u : STORE == ANN_STORE_E4M3 ? 1u : 2u);
+    const uint32_t row_bytes = (uint32_t)a.d_pad * ES;
+    const uint32_t cpr = row_bytes / 16u;
     int off[10];
     cluster_smem_bytes(a.qfloats, a.Lcap, a.Ccap, a.hash_bits, a.M, off);
     float *qv = reinterpret_cast<float *>(smem + off[0]);
@@ -64,9 +74,14 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     entry_t *uni = reinterpret_cast<entry_t *>(smem + off[6]);
     unsigned char *dup = smem + off[7];
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + off[8]);
-    int *act = reinterpret_cast<int *>(smem + off[9]);
+    int *sel_id = reinterpret_cast<int *>(smem + off[9]);
+    int *sel_pos = sel_id + a.M;
     const int H = 1 << a.hash_bits;
     const int R = a.R;
+    const int slots_w = (a.M * R + NW - 1) / NW;
+    uint2 *fresh = reinterpret_cast<uint2 *>(cand) + (size_t)warp * slots_w;
+    const uint32_t r_recip = 0xFFFFFFFFu / (uint32_t)R + 1u;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     // one query per cluster; identical in every CTA of the cluster
     const int item = (int)(blockIdx.x / C);
@@ -94,153 +109,115 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
 
     if (tid == 0) {
         ctl.t0 = global_ns();
-        ctl.steps = ctl.expansions = ctl.resets = ctl.dropped = 0;
-        ctl.evals = 1;
+        ctl.steps = ctl.expansions = ctl.dropped = 0;
         ctl.pub_n[0] = ctl.pub_n[1] = 0;
+        ctl.pub_fresh[0] = ctl.pub_fresh[1] = 0;
+        ctl.unsafe = 0;
+        ctl.first_un = 0;
+        ctl.wevals = 0;
     }
     const float *qg = a.queries + (size_t)qi * a.d;
     for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
-    for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
-    if (tid == 0) cand[0] = (entry_t)(uint32_t)a.entry;
+    {
+        const uint32_t empty = a.ways ? 0u : kEmptySlot;
+        for (int i = tid; i < H; i += NT) table[i] = empty;
+    }
+    if (tid == 0) fresh[0] = make_uint2((uint32_t)a.entry, (uint32_t)a.entry);
     __syncthreads();
     // the entry point: every CTA computes the same key; its owner marks it visited
-    compute_keys<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, 1);
+    if (warp == 0)
+        warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, 1, a.team_lanes, kEmptyEntry, uni,
+                                         &ctl.pub_n[1]);
     __syncthreads();
     if (tid == 0) {
-        Q[0] = cand[0];
-        ctl.qlen = 1;
-        ctl.hash_count = 0;
-        if ((int)(a.entry % C) == rank) {
-            visited_insert(table, a.hash_bits, (uint32_t)a.entry);
-            ctl.hash_count = 1;
-        }
+        Q[0] = uni[0];
+        ctl.pub_n[1] = 0;
+        if ((int)(a.entry % C) == rank) visit_set(table, a, (uint32_t)a.entry);
     }
     __syncthreads();
 
     int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
     int step = 0;
+    int qlen = 1;
     for (;;) {
-        const int qlen = ctl.qlen;
-        if (ctl.hash_count * 2 > H) {  // forget own vertices when half full (keep own queued ids)
-            for (int i = tid; i < H; i += NT) table[i] = kEmptySlot;
-            __syncthreads();
-            for (int i = tid; i < qlen; i += NT) {
-                const uint32_t u = entry_id(Q[i]);
-                if ((int)(u % C) == rank) visited_insert(table, a.hash_bits, u);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int own = 0;
-                for (int i = 0; i < qlen; ++i) own += (int)(entry_id(Q[i]) % C) == rank;
-                ctl.hash_count = own;
-                ctl.resets++;
-            }
-        }
+        const int par = step & 1;
+        // --- select (every CTA, identical): warp 0 takes the first Mcur unchecked entries
         if (warp == 0) {
-            int found = 0;
-            for (int b = 0; b < qlen && found < Mcur; b += 32) {
+            int found = 0, last_pos = -1;
+            for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
                 const int i = b + lane;
                 const entry_t e = i < qlen ? Q[i] : kChecked;
                 const bool un = !(e & kChecked);
                 const unsigned bal = __ballot_sync(kFull, un);
-                const int r = found + __popc(bal & ((1u << lane) - 1u));
-                if (un && r < Mcur) {
-                    act[r] = (int)entry_id(e);
-                    Q[i] = e | kChecked;
+                const int r = found + __popc(bal & lt_mask);
+                const bool take = un && r < Mcur;
+                if (take) {
+                    sel_id[r] = (int)entry_id(e);
+                    sel_pos[r] = i;
                 }
+                const unsigned tb = __ballot_sync(kFull, take);
+                if (tb) last_pos = b + 31 - __clz(tb);
                 found += __popc(bal);
             }
             if (lane == 0) {
-                ctl.nact = found < Mcur ? found : Mcur;
-                ctl.ncand = 0;
-                ctl.nloc = 0;
+                ctl.sel_found = found;
+                ctl.sel_last = last_pos;
             }
         }
         __syncthreads();
-        const int nact = ctl.nact;
+        const int found = ctl.sel_found;
+        const int nact = found < Mcur ? found : Mcur;
         if (nact == 0) break;  // identical in every CTA: all leave the loop at the same step
         step++;
-        const int par = step & 1;
-        if (tid == 0) {
-            ctl.steps++;
-            ctl.expansions += nact;
-        }
-        // own neighbours of the selected vertices -> visited filter -> local candidates
-        const int total = nact * R;
-        for (int b = warp * 32; b < total; b += NT) {
-            const int i = b + lane;
-            int u = -1;
-            if (i < total) {
-                const int aidx = i / R, r = i - aidx * R;
-                u = __ldg(a.adj + (size_t)act[aidx] * R + r);
-                if (u >= 0 && (u % C) != rank) u = -1;
-            }
-            const bool fresh = u >= 0 && visited_insert(table, a.hash_bits, (uint32_t)u) != 0;
-            const unsigned bal = __ballot_sync(kFull, fresh);
-            int basepos = 0;
-            if (lane == 0 && bal) basepos = atomicAdd(&ctl.ncand, __popc(bal));
-            basepos = __shfl_sync(kFull, basepos, 0);
-            if (fresh) {
-                cand[basepos + __popc(bal & ((1u << lane) - 1u))] = (entry_t)(uint32_t)u;
-                if (a.l2_prefetch) prefetch_row_l2(a.base, row_bytes, (uint32_t)u);
-            }
-        }
-        __syncthreads();
-        const int nc = ctl.ncand;
-        if (tid == 0) ctl.hash_count += nc;
+
+        // --- this CTA's own neighbours: adjacency -> visited set -> fresh lists -> distances -> published
+        const int nf = expand_step<NW>(a, table, sel_id, nact, r_recip, row_bytes, fresh, nullptr, nullptr, C, rank,
+                                       &ctl.unsafe);
+        if (lane == 0 && nf) atomicAdd(&ctl.wevals, nf);
         const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
-        if (nc > 0)
-            compute_keys_teams<STORE, NT>(a.base, a.scales, a.d_pad, a.metric, qv, cand, nc, a.team_lanes, limit,
-                                          pub[par], &ctl.nloc);
+        if (!gather_fixed<STORE, L2>(a.base, a.scales, cpr, a.team_lanes, qv, nullptr, fresh, nf, 0, 1, limit,
+                                     pub[par], &ctl.pub_n[par]))
+            warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, nf, a.team_lanes, limit, pub[par],
+                                             &ctl.pub_n[par]);
         __syncthreads();
-        if (tid == 0) {
-            ctl.pub_n[par] = ctl.nloc;
-            ctl.pub_fresh[par] = nc;
-        }
+        if (tid == 0) ctl.pub_unsafe[par] = ctl.unsafe;
         cluster.sync();  // every CTA's survivors of this step are published
         // gather the union in rank order (the same order in every CTA)
-        int tot = 0;
+        int tot = 0, any_unsafe = 0;
         for (int r = 0; r < C; ++r) {
-            const int *rn = cluster.map_shared_rank(&ctl.pub_n[par], r);
+            const int n = *cluster.map_shared_rank(&ctl.pub_n[par], r);
             const entry_t *rp = cluster.map_shared_rank(pub[par], r);
-            const int n = *rn;
             for (int i = tid; i < n; i += NT) uni[tot + i] = rp[i];
             tot += n;
-            if (tid == 0 && rank == 0) ctl.evals += *cluster.map_shared_rank(&ctl.pub_fresh[par], r);
+            any_unsafe |= *cluster.map_shared_rank(&ctl.pub_unsafe[par], r);
+        }
+        if (tid < nact) Q[sel_pos[tid]] |= kChecked;  // the selection is taken: mark it
+        if (tid == 0) {
+            ctl.pub_n[par ^ 1] = 0;  // the next step's list (every CTA read it before this step's barrier)
+            ctl.steps++;
+            ctl.expansions += nact;
+            ctl.first_un = ctl.sel_last + 1;
         }
         __syncthreads();
         if (tot > 0) {
-            if (tot <= 32) {
-                if (warp == 0) {
-                    entry_t e = lane < tot ? uni[lane] : kEmptyEntry;
-                    e = warp_sort32(e);
-                    uni[lane] = e;
-                }
-                __syncthreads();
-            } else {
-                int P = 64;
-                while (P < tot) P <<= 1;
-                for (int i = tot + tid; i < P; i += NT) uni[i] = kEmptyEntry;
-                __syncthreads();
-                block_bitonic_sort<NT>(uni, P);
-            }
-            long long dropped = 0;
-            const int nl = block_merge_dedupe<NT>(Q, qlen, uni, tot, L, Qn, dup, &ctl.anydup, &dropped);
-            if (tid == 0) {
-                ctl.dropped += dropped;
-                ctl.qlen = nl;
-            }
+            const int ncl = sort_dedupe_merge<NT>(Q, qlen, uni, tot, cand, Qn, L, any_unsafe != 0, dup, &ctl.anydup,
+                                                  &ctl.dropped, &ctl.first_un);
+            qlen = min(L, qlen + ncl);
             entry_t *t = Q;
             Q = Qn;
             Qn = t;
+        } else {
+            __syncthreads();
         }
-        __syncthreads();
         if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
     }
 
+    // distance evaluations of the whole cluster: every CTA's own fresh vertices (read before the last barrier)
+    long long evals = 1;
+    if (rank == 0 && tid == 0)
+        for (int r = 0; r < C; ++r) evals += *cluster.map_shared_rank(&ctl.wevals, r);
     // output from rank 0 (optionally re-ranked with FP32 rows)
     if (rank == 0) {
-        const int qlen = ctl.qlen;
         const entry_t *res = Q;
         if (a.rerank) {
             for (int i = tid; i < qlen; i += NT) {
@@ -248,14 +225,23 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
                 cand[i] = (entry_t)id;
                 if (a.l2_prefetch) prefetch_row_l2(a.base32, (uint32_t)a.d_pad32 * 4u, id);
             }
+            if (tid == 0) ctl.rr_n = 0;
             __syncthreads();
-            compute_keys<ANN_STORE_F32, NT>(a.base32, nullptr, a.d_pad32, a.metric, qv, cand, qlen);
-            int P = 32;
-            while (P < qlen) P <<= 1;
-            for (int i = qlen + tid; i < P; i += NT) cand[i] = kEmptyEntry;
+            if (!gather_fixed<ANN_STORE_F32, L2>(a.base32, nullptr, (uint32_t)a.d_pad32 / 4u, a.team_lanes32, qv,
+                                                 cand, nullptr, qlen, warp, NW, kEmptyEntry, uni, &ctl.rr_n))
+                compute_keys_teams_m<ANN_STORE_F32, NT, L2, 2>(a.base32, nullptr, a.d_pad32, qv, cand, qlen,
+                                                               a.team_lanes32, kEmptyEntry, uni, &ctl.rr_n);
             __syncthreads();
-            block_bitonic_sort<NT>(cand, P);
-            res = cand;
+            if (k <= 32) {
+                res = block_topk<NT>(uni, qlen, k, cand, uni);
+            } else {
+                int P = 32;
+                while (P < qlen) P <<= 1;
+                for (int i = qlen + tid; i < P; i += NT) uni[i] = kEmptyEntry;
+                __syncthreads();
+                block_bitonic_sort<NT>(uni, P);
+                res = uni;
+            }
         }
         int64_t *oid = a.out_ids + (size_t)qi * a.k;
         float *odist = a.out_dists + (size_t)qi * a.k;
@@ -272,8 +258,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
             ann_query_stats st;
             st.steps = ctl.steps;
             st.expansions = ctl.expansions;
-            st.evals = ctl.evals;
-            st.hash_resets = ctl.resets;
+            st.evals = evals;
+            st.hash_resets = 0;
             st.dup_dropped = ctl.dropped;
             st.merges = 0;
             st.t_start_ns = ctl.t0;
@@ -291,7 +277,7 @@ int cluster_smem_size(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap) 
 
 template <int NT, int STORE>
 static cudaError_t claunch_t(const SearchArgs &a, int smem, int csize, cudaStream_t s) {
-    auto fn = cluster_search_kernel<NT, STORE>;
+    auto fn = a.metric == ANN_METRIC_L2 ? cluster_search_kernel<NT, STORE, true> : cluster_search_kernel<NT, STORE, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

@@ -119,15 +119,22 @@ template <> struct Chunk<ANN_STORE_E4M3> {
     }
 };
 
-// Ask L2 for one row: one prefetch.global.L2 per 128-byte line it touches.
-// No completion is tracked and no register is held, so every row of a step
-// can be in flight at once. Each lane names its own row: a bulk prefetch
-// (cp.async.bulk.prefetch.L2) takes a warp-uniform address, so rows that
-// differ per lane would be issued one lane at a time.
+// Ask L2 for one row. No completion is tracked and no register is held, so
+// every row of a step can be in flight at once. Each lane names its own row.
+// Rows of up to 1 KB take one prefetch.global.L2 per 128-byte line they touch
+// (at most 9 instructions, issued by every lane at once); longer rows take
+// one bulk prefetch (cp.async.bulk.prefetch.L2), whose address is
+// warp-uniform, so lanes with different rows issue it one after another --
+// still fewer instructions than a line at a time for a 2-4 KB row.
 __device__ __forceinline__ void prefetch_row_l2(const void *rows, uint32_t row_bytes, uint32_t id) {
-    const uintptr_t p = reinterpret_cast<uintptr_t>(rows) + (size_t)id * row_bytes;
-    const uintptr_t end = p + row_bytes;
-    for (uintptr_t a = p & ~uintptr_t(127); a < end; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    const char *row = static_cast<const char *>(rows) + (size_t)id * row_bytes;
+    const size_t p = __cvta_generic_to_global(row);  // the .global state space address of the row
+    if (row_bytes > 1024) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(row_bytes) : "memory");
+        return;
+    }
+    const size_t end = p + row_bytes;
+    for (size_t a = p & ~size_t(127); a < end; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
 // Ask L2 for one contiguous range (16-byte aligned start, bytes a multiple
@@ -687,19 +694,22 @@ __device__ int block_merge_dedupe(entry_t *Q, int qlen, entry_t *C, int nc, int 
 // Keys of the nf candidates fr[0..nf) (one warp): fr[c].x is the vertex id
 // and fr[c].y the row that holds its vector (the id itself, or a row of a
 // neighbour group). Teams of 2^lts lanes per row; each lane walks its own
-// 16-byte chunks of the row, G of them in flight. Candidates below `limit`
-// are appended to out[] through the shared counter *out_n. No barrier.
+// 16-byte chunks of the row, G of them in flight. The warp takes passes
+// pass_begin, pass_begin + pass_step, ... of 32 >> lts candidates.
+// Candidates below `limit` are appended to out[] through the shared counter
+// *out_n. No barrier.
 template <int STORE, int G, bool L2>
 __device__ __forceinline__ void warp_keys_append_m(const void *rows, const float *scales, uint32_t cpr,
                                                    const float *qv, const uint2 *fr, int nf, int lts,
-                                                   entry_t limit, entry_t *out, int *out_n) {
+                                                   entry_t limit, entry_t *out, int *out_n, int pass_begin = 0,
+                                                   int pass_step = 1) {
     constexpr int EPC = Chunk<STORE>::kElems;
     const int lane = threadIdx.x & 31;
     const int ts = 1 << lts, rpw = 32 >> lts;
     const int team = lane >> lts, tl = lane & (ts - 1);
     constexpr bool l2 = L2;
     const uint4 *rbase = reinterpret_cast<const uint4 *>(rows);
-    for (int c0 = 0; c0 < nf; c0 += rpw) {
+    for (int c0 = pass_begin * rpw; c0 < nf; c0 += pass_step * rpw) {
         const int c = c0 + team;
         const bool valid = c < nf;
         const uint2 f = valid ? fr[c] : make_uint2(0u, 0u);
@@ -815,6 +825,187 @@ __device__ __forceinline__ bool gather_fixed(const void *rows, const float *scal
     }
 #undef ANN_FIXED
     return false;
+}
+
+// ------------------------------------------------------- one search step
+
+// One insert into the query's visited set, whichever form it has: 0 = was
+// present, 1 = inserted, 2 or 3 = inserted while another vertex may have been
+// forgotten (probe limit, eviction).
+__device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, uint32_t id) {
+    if (a.ways == 3) return visited_assoc<3>(table, a.hash_bits, a.tag_bits, id);
+    if (a.ways == 2) return visited_assoc<2>(table, a.hash_bits, a.tag_bits, id);
+    if (a.visited_mode == 0) return visited_insert(table, a.hash_bits, id);
+    if (a.slot_bytes == 1) return visited_tag<1>(table, a.hash_bits, a.tag_bits, id);
+    if (a.slot_bytes == 2) return visited_tag<2>(table, a.hash_bits, a.tag_bits, id);
+    return visited_exchange(table, a.hash_bits, id);
+}
+
+// One warp's share of a step's expansion: the step's nact * R adjacency
+// slots (slot i is slot i mod R of selected vertex sel_id[i / R]; r_recip =
+// ceil(2^32 / R) makes i / R one umulhi) are split evenly over the NW warps.
+// Each neighbour that the visited set did not hold is appended, as an (id,
+// row) pair, to this warp's list `fresh` (or, if `block` is given, to one list
+// for the CTA through the counter *block_n), and its row is asked of L2. With
+// owners > 1 (a power of two) only vertices u with u mod owners == owner are
+// inserted and listed: the vertices this CTA of a cluster owns. A hot vertex
+// of a neighbour grouping gives its neighbours' rows in its group block
+// (one bulk prefetch for the block). Sets *unsafe if an insert may have
+// forgotten another vertex. Returns the fresh vertices this warp found.
+template <int NW>
+__device__ __forceinline__ int expand_step(const SearchArgs &a, uint32_t *table, const int *sel_id, int nact,
+                                           uint32_t r_recip, uint32_t row_bytes, uint2 *fresh, uint2 *block,
+                                           int *block_n, int owners, int owner, int *unsafe) {
+    constexpr int KA = 4;  // slots per lane whose loads are in flight together
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int R = a.R;
+    const int total = nact * R;
+    const int per = (total + NW - 1) / NW;
+    const int beg = warp * per, end = min(beg + per, total);
+    int nf = 0;
+    for (int b0 = beg; b0 < end; b0 += 32 * KA) {
+        int u[KA];
+        uint32_t urow[KA];  // the row holding u's vector: u, or its copy in a neighbour group
+#pragma unroll
+        for (int kk = 0; kk < KA; ++kk) {
+            const int i = b0 + kk * 32 + lane;
+            u[kk] = -1;
+            urow[kk] = 0;
+            if (i < end) {
+                const uint32_t j = __umulhi((uint32_t)i, r_recip);
+                const uint32_t slot = (uint32_t)i - j * (uint32_t)R;
+                const uint32_t v = (uint32_t)sel_id[j];
+                u[kk] = __ldg(a.adj + (size_t)v * (uint32_t)R + slot);
+                if (owners > 1 && u[kk] >= 0 && ((uint32_t)u[kk] & (uint32_t)(owners - 1)) != (uint32_t)owner)
+                    u[kk] = -1;
+                urow[kk] = (uint32_t)u[kk];
+                if (a.hot_slot) {
+                    // a hot vertex: its neighbours' rows lie in one block after the base rows, in adjacency
+                    // order; one bulk prefetch (from the lane with its first slot) asks L2 for the block
+                    const int hs = __ldg(a.hot_slot + v);
+                    if (hs >= 0) {
+                        const uint32_t r0 = (uint32_t)a.n + (uint32_t)hs * (uint32_t)R;
+                        urow[kk] = r0 + slot;
+                        if (slot == 0 && a.l2_prefetch && a.group_prefetch == 0)
+                            prefetch_range_l2(static_cast<const char *>(a.base) + (size_t)r0 * row_bytes,
+                                              (uint32_t)R * row_bytes);
+                    }
+                }
+            }
+        }
+        unsigned fr = 0;  // bit kk: u[kk] was not in the visited set
+        bool forgot = false;
+#pragma unroll
+        for (int kk = 0; kk < KA; ++kk) {
+            if (u[kk] >= 0) {
+                const int ins = visit_set(table, a, (uint32_t)u[kk]);
+                if (ins != 0) fr |= 1u << kk;
+                if (ins >= 2) forgot = true;
+            }
+        }
+        if (forgot) *unsafe = 1;  // a vertex may have been forgotten: repeats possible
+        const int cnt = __popc(fr);
+        int incl = cnt;  // inclusive scan of the per-lane counts
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int wtot = __shfl_sync(kFull, incl, 31);
+        int pos;
+        if (block) {  // one list for the whole CTA
+            int base = 0;
+            if (lane == 31 && wtot) base = atomicAdd(block_n, wtot);
+            pos = __shfl_sync(kFull, base, 31) + incl - cnt;
+        } else {
+            pos = nf + incl - cnt;
+        }
+        uint2 *dst = block ? block : fresh;
+#pragma unroll
+        for (int kk = 0; kk < KA; ++kk) {
+            if (fr >> kk & 1u) {
+                dst[pos++] = make_uint2((uint32_t)u[kk], urow[kk]);
+                if (a.l2_prefetch && (urow[kk] < (uint32_t)a.n || a.group_prefetch))
+                    prefetch_row_l2(a.base, row_bytes, urow[kk]);
+            }
+        }
+        nf += wtot;
+    }
+    return nf;
+}
+
+// The ns (> 0) survivors in surv, sorted by (key, id) (one warp for 32 or
+// fewer, warp runs plus binary-search ranks into `scratch` up to NT, else a
+// bitonic sort in place), are merged into the sorted queue Q[0..qlen): when
+// `unsafe` (the visited set may have forgotten a vertex) survivors whose id
+// is already queued, or repeated, are dropped first (counted in *dropped).
+// The first min(L, qlen + kept) entries go to Qn by merge path. *first_un
+// (every entry before it is checked) is lowered to the first survivor's new
+// rank. Every thread calls it with the same arguments; it ends with a
+// barrier. Returns the number of survivors kept.
+template <int NT>
+__device__ __forceinline__ int sort_dedupe_merge(const entry_t *Q, int qlen, entry_t *surv, int ns, entry_t *scratch,
+                                                 entry_t *Qn, int L, bool unsafe, unsigned char *dup, int *anydup,
+                                                 long long *dropped, int *first_un) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    entry_t *srt = surv;
+    if (ns <= 32) {
+        if (warp == 0) {
+            entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
+            e = warp_sort32(e);
+            surv[lane] = e;
+        }
+        __syncthreads();
+    } else if (ns > 64 && ns <= NT) {
+        // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
+        block_rank_sort<NT>(surv, ns, scratch);
+        srt = scratch;
+    } else {
+        int P = 64;
+        while (P < ns) P <<= 1;
+        for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
+        __syncthreads();
+        block_bitonic_sort<NT>(surv, P);
+    }
+    int ncl = ns;
+    if (unsafe) {
+        int any = 0;
+        for (int j = tid; j < ns; j += NT) {
+            const entry_t c = srt[j];
+            bool d = (j > 0 && srt[j - 1] == c);
+            if (!d) {
+                const int pos = count_below(Q, qlen, c);
+                d = pos < qlen && (Q[pos] & kMask) == c;
+            }
+            dup[j] = d;
+            any |= d;
+        }
+        if (__syncthreads_or(any)) {
+            if (warp == 0) {
+                int outp = 0;
+                for (int b = 0; b < ns; b += 32) {
+                    const int j = b + lane;
+                    const bool keep = j < ns && !dup[j];
+                    const entry_t c = j < ns ? srt[j] : 0ull;
+                    const unsigned bal = __ballot_sync(kFull, keep);
+                    if (keep) srt[outp + __popc(bal & ((1u << lane) - 1u))] = c;
+                    outp += __popc(bal);
+                }
+                if (lane == 0) *anydup = outp;
+            }
+            __syncthreads();
+            ncl = *anydup;
+            if (tid == 0) *dropped += ns - ncl;
+        }
+    }
+    // the first survivor's rank among the old entries bounds the new queue's checked prefix
+    if (tid == 0 && ncl > 0) {
+        const int p0 = count_below(Q, qlen, srt[0]);
+        if (p0 < *first_un) *first_un = p0;
+    }
+    block_merge_path<NT>(Q, qlen, srt, ncl, Qn, L);
+    __syncthreads();  // the new queue is complete; nothing of the old one is read again
+    return ncl;
 }
 
 }  // namespace ann

@@ -9,12 +9,12 @@
 // One step, inside one CTA of NW warps:
 //   select   warp 0 takes the first min(M_s, #unchecked) unchecked entries of
 //            the sorted queue by ballot + popc, starting past a prefix known to
-//            be checked; the selected vertex of rank r goes to warp r mod NW;
-//   expand   each warp reads the adjacency rows of its own selected vertices
-//            (one lane per slot, coalesced int32 rows), inserts each
-//            neighbour into the shared visited set and appends the fresh ones
-//            to its own list (one warp scan per batch of rows), asking L2 for
-//            each fresh row as it goes;
+//            be checked;
+//   expand   the step's M_s * R adjacency slots are split evenly over the
+//            warps (one lane per slot, coalesced int32 rows); each warp
+//            inserts its neighbours into the shared visited set and appends
+//            the fresh ones to its own list (one warp scan per batch of
+//            slots), asking L2 for each fresh row as it goes;
 //   distance each warp gathers its own fresh rows with teams of lanes (16-byte
 //            non-caching loads, shuffle reduction) and appends every
 //            candidate below the queue's L-th entry to the CTA's survivor
@@ -38,6 +38,7 @@ namespace ann {
 
 struct Ctrl {
     int ns[2];     // survivors appended in the step of this parity
+    int nfresh[2]; // block gather: fresh vertices appended in the step of this parity
     int hash_count;
     int do_reset;  // open addressing: the table is half full, reset it before the next select
     int anydup;
@@ -50,18 +51,6 @@ struct Ctrl {
     long long steps, expansions, evals, resets, dropped, t0;
     long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
 };
-
-// One insert into the query's visited set, whichever form it has: 0 = was
-// present, 1 = inserted, 2 or 3 = inserted while another vertex may have been
-// forgotten (probe limit, eviction).
-__device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, uint32_t id) {
-    if (a.ways == 3) return visited_assoc<3>(table, a.hash_bits, a.tag_bits, id);
-    if (a.ways == 2) return visited_assoc<2>(table, a.hash_bits, a.tag_bits, id);
-    if (a.visited_mode == 0) return visited_insert(table, a.hash_bits, id);
-    if (a.slot_bytes == 1) return visited_tag<1>(table, a.hash_bits, a.tag_bits, id);
-    if (a.slot_bytes == 2) return visited_tag<2>(table, a.hash_bits, a.tag_bits, id);
-    return visited_exchange(table, a.hash_bits, id);
-}
 
 template <int NT, int STORE, bool L2>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(const SearchArgs a) {
@@ -83,12 +72,14 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     uint32_t *table = reinterpret_cast<uint32_t *>(smem + lay.hash_off);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
-    const int SR = (R + 31) >> 5;                 // 32-lane parts per adjacency row
-    const int rows_w = (a.M + NW - 1) / NW;      // most rows one warp expands in a step
-    // this warp's selected vertices (ids, queue positions) and its fresh vertices
-    int *sel_id = reinterpret_cast<int *>(smem + lay.act_off) + warp * rows_w;
-    int *sel_pos = reinterpret_cast<int *>(smem + lay.act_off) + NW * rows_w + warp * rows_w;
-    uint2 *fresh = reinterpret_cast<uint2 *>(cand) + (size_t)warp * rows_w * R;  // (id, row) pairs
+    // the step's selected vertices (ids, queue positions), and this warp's fresh vertices: a step's M * R
+    // adjacency slots are split evenly over the warps, slot i of the step being slot i mod R of the
+    // (i / R)-th selected vertex; i / R = umulhi(i, ceil(2^32 / R)), exact while i < 2^32 / R^2
+    int *sel_id = reinterpret_cast<int *>(smem + lay.act_off);
+    int *sel_pos = sel_id + a.M;
+    const int slots_w = (a.M * R + NW - 1) / NW;  // most slots one warp expands in a step
+    uint2 *fresh = reinterpret_cast<uint2 *>(cand) + (size_t)warp * slots_w;  // (id, row) pairs
+    const uint32_t r_recip = 0xFFFFFFFFu / (uint32_t)R + 1u;
 
     for (;;) {
         if (tid == 0) {
@@ -139,6 +130,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
         }
         if (tid == 0) {
             ctl.ns[0] = ctl.ns[1] = 0;
+            ctl.nfresh[0] = ctl.nfresh[1] = 0;
             fresh[0] = make_uint2((uint32_t)a.entry, (uint32_t)a.entry);
         }
         __syncthreads();
@@ -185,10 +177,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             }
             const int par = step & 1;
             // --- select: warp 0 takes the first Mcur unchecked entries (rank order) of the stable queue
-            // (entries before first_un are all checked) and hands rank r to warp r mod NW
-            int found = 0, my_rows = 0, last_pos = -1;
+            // (entries before first_un are all checked)
+            int found = 0, last_pos = -1;
             if (warp == 0) {
-                int *sid0 = reinterpret_cast<int *>(smem + lay.act_off);
                 for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
                     const int i = b + lane;
                     const entry_t e = i < qlen ? Q[i] : kChecked;
@@ -197,8 +188,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                     const int r = found + __popc(bal & lt_mask);
                     const bool take = un && r < Mcur;
                     if (take) {
-                        sid0[(r % NW) * rows_w + r / NW] = (int)entry_id(e);
-                        sid0[NW * rows_w + (r % NW) * rows_w + r / NW] = i;
+                        sel_id[r] = (int)entry_id(e);
+                        sel_pos[r] = i;
                     }
                     const unsigned tb = __ballot_sync(kFull, take);
                     if (tb) last_pos = b + 31 - __clz(tb);
@@ -214,74 +205,14 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             last_pos = ctl.sel_last;
             const int nact = found < Mcur ? found : Mcur;
             if (nact == 0) break;  // no unchecked vertex left (identical in every warp)
-            my_rows = nact > warp ? (nact - warp + NW - 1) / NW : 0;
-            __syncwarp();
             ANN_PHASE(0)
             step++;
 
-            // --- expand this warp's rows: adjacency -> visited set -> fresh list (+ L2 prefetch)
-            int nf = 0;
-            {
-                constexpr int KA = 4;  // row parts whose loads are in flight together
-                const int units = my_rows * SR;
-                for (int t0 = 0; t0 < units; t0 += KA) {
-                    int u[KA];
-                    uint32_t urow[KA];  // the row holding u's vector: u, or its copy in a neighbour group
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) {
-                        const int t = t0 + kk;
-                        u[kk] = -1;
-                        urow[kk] = 0;
-                        if (t < units) {
-                            const int j = SR == 1 ? t : t / SR;
-                            const int slot = (t - j * SR) * 32 + lane;
-                            const uint32_t v = (uint32_t)sel_id[j];
-                            if (slot < R) u[kk] = __ldg(a.adj + (size_t)v * (uint32_t)R + slot);
-                            urow[kk] = (uint32_t)u[kk];
-                            if (a.hot_slot) {
-                                // a hot vertex: its neighbours' rows lie in one block after the base rows, in
-                                // adjacency order; one bulk prefetch (from one lane) asks L2 for the block
-                                const int hs = __ldg(a.hot_slot + v);
-                                if (hs >= 0) {
-                                    const uint32_t r0 = (uint32_t)a.n + (uint32_t)hs * (uint32_t)R;
-                                    urow[kk] = r0 + (uint32_t)slot;
-                                    if (lane == 0 && a.l2_prefetch && slot == lane && a.group_prefetch == 0)
-                                        prefetch_range_l2(static_cast<const char *>(a.base) + (size_t)r0 * row_bytes,
-                                                          (uint32_t)R * row_bytes);
-                                }
-                            }
-                        }
-                    }
-                    unsigned fr = 0;  // bit kk: u[kk] was not in the visited set
-                    bool forgot = false;
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) {
-                        if (u[kk] >= 0) {
-                            const int ins = visit_set(table, a, (uint32_t)u[kk]);
-                            if (ins != 0) fr |= 1u << kk;
-                            if (ins >= 2) forgot = true;
-                        }
-                    }
-                    if (forgot) ctl.unsafe = 1;  // a vertex may have been forgotten: repeats possible
-                    const int cnt = __popc(fr);
-                    int incl = cnt;  // inclusive scan of the per-lane counts
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const int v = __shfl_up_sync(kFull, incl, off);
-                        if (lane >= off) incl += v;
-                    }
-                    int pos = nf + incl - cnt;
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) {
-                        if (fr >> kk & 1u) {
-                            fresh[pos++] = make_uint2((uint32_t)u[kk], urow[kk]);
-                            if (a.l2_prefetch && (urow[kk] < (uint32_t)a.n || a.group_prefetch))
-                                prefetch_row_l2(a.base, row_bytes, urow[kk]);
-                        }
-                    }
-                    nf += __shfl_sync(kFull, incl, 31);
-                }
-            }
+            // --- expand this warp's share of the step's adjacency slots: adjacency -> visited set -> fresh
+            // list (+ L2 prefetch)
+            const int nf = expand_step<NW>(a, table, sel_id, nact, r_recip, row_bytes, fresh,
+                                           a.block_gather ? reinterpret_cast<uint2 *>(cand) : nullptr,
+                                           &ctl.nfresh[par], 1, 0, &ctl.unsafe);
             __syncwarp();
             if (lane == 0) {
                 if (nf) {
@@ -294,83 +225,41 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             // --- distances of this warp's fresh rows; only candidates below the L-th queued entry survive
             const int L = ctl.L;
             const entry_t limit = qlen >= L ? (Q[L - 1] & kMask) : kEmptyEntry;
-            // four chunks in flight per lane (one 128-d BF16 row per 4-lane team in one round trip)
-            if (!gather_fixed<STORE, L2>(a.base, a.scales, cpr, a.team_lanes, qv, nullptr, fresh, nf, 0, 1, limit,
-                                         surv, &ctl.ns[par]))
-                warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, fresh, nf, a.team_lanes, limit, surv,
-                                                 &ctl.ns[par]);
+            // four chunks in flight per lane (one 128-d BF16 row per 4-lane team in one round trip); each warp
+            // gathers its own list, or, with a block gather (long rows: few per warp), every warp takes every
+            // NW-th pass of one list for the CTA
+            {
+                const uint2 *gl = fresh;
+                int gn = nf, gb = 0, gs = 1;
+                if (a.block_gather) {
+                    __syncthreads();  // the CTA's list is complete
+                    gl = reinterpret_cast<const uint2 *>(cand);
+                    gn = ctl.nfresh[par];
+                    gb = warp;
+                    gs = NW;
+                }
+                if (!gather_fixed<STORE, L2>(a.base, a.scales, cpr, a.team_lanes, qv, nullptr, gl, gn, gb, gs, limit,
+                                             surv, &ctl.ns[par]))
+                    warp_keys_append_m<STORE, 4, L2>(a.base, a.scales, cpr, qv, gl, gn, a.team_lanes, limit, surv,
+                                                     &ctl.ns[par], gb, gs);
+            }
             __syncthreads();
             ANN_PHASE(2)
             const int ns = ctl.ns[par];
-            if (lane < my_rows) Q[sel_pos[lane]] |= kChecked;  // the selection is taken: mark it
+            if (tid < nact) Q[sel_pos[tid]] |= kChecked;  // the selection is taken: mark it
             if (tid == 0) {
-                ctl.ns[par ^ 1] = 0;  // next step's counter (last read before this step's barrier)
+                ctl.ns[par ^ 1] = 0;  // next step's counters (last read before this step's barrier)
+                ctl.nfresh[par ^ 1] = 0;
                 ctl.steps++;
                 ctl.expansions += nact;
                 ctl.first_un = last_pos + 1;
                 ctl.do_reset = a.visited_mode == 0 && ctl.hash_count * 2 > H;
             }
             if (ns > 0) {
-                // --- sort the survivors by (key, id) into srt
-                entry_t *srt = surv;
-                if (ns <= 32) {
-                    if (warp == 0) {
-                        entry_t e = lane < ns ? surv[lane] : kEmptyEntry;
-                        e = warp_sort32(e);
-                        surv[lane] = e;
-                    }
-                    __syncthreads();
-                } else if (ns > 64 && ns <= NT) {
-                    // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
-                    block_rank_sort<NT>(surv, ns, cand);  // the fresh lists are not needed any more
-                    srt = cand;
-                } else {
-                    int P = 64;
-                    while (P < ns) P <<= 1;
-                    for (int i = ns + tid; i < P; i += NT) surv[i] = kEmptyEntry;
-                    __syncthreads();
-                    block_bitonic_sort<NT>(surv, P);
-                }
-                int ncl = ns;
-                if (ctl.unsafe) {
-                    // --- drop ids already queued or repeated (only after the visited set forgot)
-                    int any = 0;
-                    for (int j = tid; j < ns; j += NT) {
-                        const entry_t c = srt[j];
-                        bool d = (j > 0 && srt[j - 1] == c);
-                        if (!d) {
-                            const int pos = count_below(Q, qlen, c);
-                            d = pos < qlen && (Q[pos] & kMask) == c;
-                        }
-                        dup[j] = d;
-                        any |= d;
-                    }
-                    if (__syncthreads_or(any)) {
-                        if (warp == 0) {
-                            int outp = 0;
-                            for (int b = 0; b < ns; b += 32) {
-                                const int j = b + lane;
-                                const bool keep = j < ns && !dup[j];
-                                const entry_t c = j < ns ? srt[j] : 0ull;
-                                const unsigned bal = __ballot_sync(kFull, keep);
-                                if (keep) srt[outp + __popc(bal & lt_mask)] = c;
-                                outp += __popc(bal);
-                            }
-                            if (lane == 0) ctl.anydup = outp;
-                        }
-                        __syncthreads();
-                        ncl = ctl.anydup;
-                        if (tid == 0) ctl.dropped += ns - ncl;
-                    }
-                }
-                // --- merge queue and survivors, truncated to L (merge path: one search per thread); the first
-                // survivor's rank among the old entries bounds the new queue's checked prefix
-                if (tid == 0 && ncl > 0) {
-                    const int p0 = count_below(Q, qlen, srt[0]);
-                    if (p0 < ctl.first_un) ctl.first_un = p0;
-                }
-                block_merge_path<NT>(Q, qlen, srt, ncl, Qn, ctl.L);
-                __syncthreads();  // the new queue is complete; nothing of the old one is read again
+                // --- sort the survivors, drop ids already queued (only after the visited set forgot a vertex),
+                // merge into the other queue buffer truncated to L
+                const int ncl = sort_dedupe_merge<NT>(Q, qlen, surv, ns, cand, Qn, ctl.L, ctl.unsafe != 0, dup,
+                                                      &ctl.anydup, &ctl.dropped, &ctl.first_un);
                 qlen = min(ctl.L, qlen + ncl);
                 entry_t *tmp = Q;
                 Q = Qn;

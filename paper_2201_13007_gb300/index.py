@@ -70,14 +70,16 @@ class Index:
     def params(mode="sync", M0=1, t=1, R_ratio=0.8, rerank=False, threads=0, hash_bits=0,
                persistent=False, k_per_query=None, L_per_query=None, M_per_query=None, stats=None,
                order=None, cluster=0, phase_cycles=None, visited_mode=0,
-               l2_prefetch=0, team_lanes=0):
+               l2_prefetch=0, team_lanes=0, patience=None, gather=0):
+        """patience=None: async walkers merge by Algorithm 2 (R_ratio); a number: by the stall count."""
         return _abi.SearchParams(mode=_abi.MODE[mode], M0=M0, t=t, R_ratio=R_ratio, rerank=int(rerank),
                                  threads=threads, hash_bits=hash_bits, persistent=int(persistent),
                                  k_per_query=_ptr(k_per_query), L_per_query=_ptr(L_per_query),
                                  M_per_query=_ptr(M_per_query), stats=_ptr(stats), order=_ptr(order),
                                  cluster=cluster, phase_cycles=_ptr(phase_cycles), visited_mode=visited_mode,
                                  l2_prefetch=l2_prefetch,
-                                 team_lanes=team_lanes)
+                                 team_lanes=team_lanes, merge_rule=0 if patience is None else 1,
+                                 patience=0.0 if patience is None else float(patience), gather=gather)
 
     def describe(self, nq, k, L, M, **kw):
         """Launch configuration of a search with these arguments (ann_search_describe)."""

@@ -472,6 +472,41 @@ def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | 
                     meta={"repaired_links": int(z["repaired"]), **spec})
 
 
+def graph_quality(adj: np.ndarray, entry: int, knn: np.ndarray | None = None, sample: int = 2000,
+                  seed: int = 9) -> dict:
+    """Structure of a fixed-degree graph, as input preparation reports it:
+    out-degree and in-degree distributions, the share of vertices reachable
+    from the entry, the share of directed edges whose reverse edge also
+    exists, and, given the exact k-NN lists, how many of each sampled
+    vertex's exact k nearest neighbours are its direct out-neighbours (the
+    "k-NN coverage" of the pruned graph)."""
+    n, R = adj.shape
+    valid = adj >= 0
+    outdeg = valid.sum(1)
+    indeg = np.bincount(adj[valid].ravel(), minlength=n)
+    reach = reachable_from(adj, entry)
+    r = _rng(seed)
+    src = r.choice(n, size=min(sample, n), replace=False)
+    back = 0
+    edges = 0
+    for v in src:
+        for u in adj[v][adj[v] >= 0]:
+            edges += 1
+            back += int(v in adj[u])
+    out = {"n": int(n), "R": int(R),
+           "out_degree": {"mean": float(outdeg.mean()), "min": int(outdeg.min()), "max": int(outdeg.max()),
+                          "full_rows": float((outdeg == R).mean())},
+           "in_degree": {"mean": float(indeg.mean()), "max": int(indeg.max()),
+                         "p99": float(np.percentile(indeg, 99)), "zero": float((indeg == 0).mean())},
+           "reachable_from_entry": float(reach.mean()),
+           "reciprocal_edges": back / max(edges, 1)}
+    if knn is not None:
+        k = knn.shape[1]
+        cov = [len(set(knn[v].tolist()) & set(adj[v][adj[v] >= 0].tolist())) / k for v in src]
+        out[f"exact_{k}nn_in_out_edges"] = float(np.mean(cov))
+    return out
+
+
 def random_graph(n, d, R, seed, metric="l2", nq=8, pad_frac=0.0, dup_frac=0.0):
     """Small adversarial inputs for tests: uniform random points, R random
     out-edges per vertex (with optional -1 padding and duplicated vectors)."""

@@ -1,6 +1,7 @@
 """Planted mistakes: each mutation of a copy of oracle.c (a wrong sign, a
 flipped tie-break, an off-by-one truncation, a dropped neighbour, a broken
-staging rule, a wrong merge test, a broken deal) must make at least one pin in
+staging rule, a wrong merge test, a broken deal, a stall count that counts
+the wrong expansions or is never reset) must make at least one pin in
 test_oracle_pins.py fail. The mutants are compiled on the CPU into a temporary
 directory; the real oracle is untouched."""
 import os
@@ -22,6 +23,8 @@ MUTATIONS = {
     "no_doubling": ("int64_t m2 = 2 * (int64_t)M;", "int64_t m2 = (int64_t)M + (M > 2);"),
     "merge_test_strict": ("return sum / (double)cnt >= (double)L * Rr;", "return sum / (double)cnt > (double)L * Rr;"),
     "deal_one_walker": ("int32_t w = dealt % M;", "int32_t w = 0;"),
+    "stall_counts_improvements": ("if (upos == L) stall[w]++;", "if (upos < L) stall[w]++;"),
+    "stall_not_reset_at_deal": ("lsn[w] = 0; U[w] = 0; stall[w] = 0; active[w] = 0;", "lsn[w] = 0; U[w] = 0; active[w] = 0;"),
     "entry_not_visited": ("    vset_add(vs, g->entry);\n    st->evals++;\n    insert_sorted(S, &len, e0);",
                           "    st->evals++;\n    insert_sorted(S, &len, e0);"),
 }

@@ -54,7 +54,7 @@ def test_golden_line_graph_traces(oracle_mod):
     adj = np.array(g["adj"], np.int32)
     q = np.array(g["query"], np.float32)
     for case in g["cases"]:
-        kw = {k: case[k] for k in ("L", "K", "M0", "M_max", "t", "R_ratio") if k in case}
+        kw = {k: case[k] for k in ("L", "K", "M0", "M_max", "t", "R_ratio", "patience") if k in case}
         tr = oracle_mod.search_trace(base, adj, g["entry"], q, algo=case["algo"], **kw)
         assert tr["ids"].tolist() == case["ids"], case["algo"]
         np.testing.assert_allclose(tr["keys"], case["keys"], rtol=1e-12)
@@ -244,6 +244,24 @@ def test_speedann_r0_is_topm_t1(oracle_mod, L, Mmax):
     for f in ("steps", "evals", "expansions"):
         np.testing.assert_array_equal(a[2][f], b[2][f])
     np.testing.assert_array_equal(a[2]["substeps"], a[2]["steps"])
+
+
+@pytest.mark.parametrize("L,Mmax", [(8, 2), (16, 4), (40, 8)])
+def test_stall_rule_limits(oracle_mod, L, Mmax):
+    """Patience 0 merges at the checker's first expansion, as Algorithm 2 with
+    R = 0 does (which is top-M with t = 1); an infinite patience never merges
+    early, as R = infinity; with one walker, patience 1 is R = 1."""
+    base, adj, q = synth.random_graph(300, 6, 5, seed=L + Mmax, nq=12)
+    cases = [(0.0, 0.0, Mmax), (float("inf"), float("inf"), Mmax),
+             # one walker: patience 1 merges at its first expansion since the deal that inserted nothing into
+             # its top L, which is when its update position first reaches L, i.e. Algorithm 2 with R = 1
+             (1.0, 1.0, 1)]
+    for pat, R, Mw in cases:
+        a = oracle_mod.search(base, adj, 0, q, algo="speedann", L=L, K=3, M0=1, M_max=Mw, patience=pat)
+        b = oracle_mod.search(base, adj, 0, q, algo="speedann", L=L, K=3, M0=1, M_max=Mw, R_ratio=R)
+        np.testing.assert_array_equal(a[0], b[0])
+        for f in ("steps", "expansions", "evals", "merges", "substeps"):
+            np.testing.assert_array_equal(a[2][f], b[2][f])
 
 
 @pytest.mark.parametrize("L", [1, 6, 32])

@@ -100,3 +100,35 @@ def test_async_rerank_and_storage(Index, sift):
     for ids, d in (a, b):
         _valid(ids.cpu().numpy(), d.cpu().numpy(), w.base, w.queries[:256])
     ix.close()
+
+
+# ------------------------------------------------- the stall-count merge test
+
+@pytest.mark.parametrize("P", [0.0, 1.0, 2.0, 3.0, float("inf")])
+@pytest.mark.parametrize("L", [16, 64, 150])
+def test_stall_rule_single_walker_is_exact(Index, oracle_mod, sift, P, L):
+    """With one walker the walk is sequential: ids, keys, distance counts,
+    expansions and merges equal the oracle's simulation under the stall rule."""
+    ids, d, st = _search(Index, sift, L, 1, 0.8, hash_bits=15, patience=P)
+    o_ids, o_keys, o_st = oracle_mod.search(sift.base, sift.adj, sift.entry, sift.queries, algo="speedann",
+                                            L=L, K=10, M0=1, M_max=1, patience=P, nthreads=8)
+    compare_exact(ids, d, o_ids, o_keys)
+    np.testing.assert_array_equal(st[:, 2], o_st["evals"])
+    np.testing.assert_array_equal(st[:, 1], o_st["expansions"])
+    np.testing.assert_array_equal(st[:, 5], o_st["merges"])
+
+
+@pytest.mark.parametrize("L,M,P", [(64, 4, 1.0), (128, 8, 2.0), (96, 16, 1.0)])
+def test_stall_rule_multi_walker_recall_matches_oracle(Index, oracle_mod, sift10k, L, M, P):
+    w = sift10k
+    ids, d, st = _search(Index, w, L, M, 0.8, patience=P)
+    _valid(ids, d, w.base, w.queries)
+    if not hasattr(test_multi_walker_recall_matches_oracle, "gt"):
+        test_multi_walker_recall_matches_oracle.gt = oracle_mod.exact_knn(w.base, w.queries, 10, nthreads=8)[0]
+    gt = test_multi_walker_recall_matches_oracle.gt
+    o_ids, _, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="speedann", L=L, K=10, M0=1,
+                                       M_max=M, patience=P, nthreads=8)
+    r_gpu = oracle_mod.recall(ids, gt).mean()
+    r_orc = oracle_mod.recall(o_ids, gt).mean()
+    print(f"stall L={L} M={M} P={P}: recall GPU {r_gpu:.5f} oracle {r_orc:.5f} gap {r_gpu - r_orc:+.5f}")
+    assert abs(r_gpu - r_orc) <= 0.002, (r_gpu, r_orc)

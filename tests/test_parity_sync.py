@@ -62,14 +62,16 @@ def test_tiny_float_parity(ann, oracle_mod, tiny, L, M):
     assert rep["match_frac"] >= 0.95, rep
 
 
+@pytest.mark.parametrize("gather", [1, 2])
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("L,M", [(16, 1), (64, 2), (100, 8), (200, 16), (64, 32)])
-def test_integer_data_bit_exact(ann, oracle_mod, sift_small, storage, L, M):
+def test_integer_data_bit_exact(ann, oracle_mod, sift_small, storage, L, M, gather):
     """0..255 integer vectors, d = 128: FP32 sums are exact, so ids and keys
-    must equal the oracle's bit for bit (BF16 holds 0..255 exactly)."""
+    must equal the oracle's bit for bit (BF16 holds 0..255 exactly), with
+    each warp gathering its own fresh rows or all warps one list."""
     _, Index, stats_dict = ann
     w = sift_small
-    ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, visited_mode=1)
+    ids, dists, st = _run(Index, w, storage=storage, L=L, M=M, hash_bits=15, visited_mode=1, gather=gather)
     o_ids, o_keys, o_st = oracle_mod.search(w.base, w.adj, w.entry, w.queries, algo="topm", L=L, K=10,
                                             M0=1, M_max=M, t=1, nthreads=8)
     compare_exact(ids, dists, o_ids, o_keys)

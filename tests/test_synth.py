@@ -34,3 +34,19 @@ def test_pruned_graph_small():
     adj, _ = synth.repair_reachability(adj, e, knn, base)
     assert adj.shape == (1500, 16)
     assert synth.reachable_from(adj, e).all()
+
+
+def test_graph_quality_on_a_hand_built_graph():
+    """A 4-cycle 0 -> 1 -> 2 -> 3 -> 0 plus the chords 0 -> 2 and 2 -> 0,
+    with an isolated vertex 4 (R = 2, -1 padded)."""
+    adj = np.array([[1, 2], [2, -1], [3, 0], [0, -1], [-1, -1]], np.int32)
+    knn = np.array([[1], [2], [3], [0], [3]], np.int32)
+    q = synth.graph_quality(adj, 0, knn, sample=5)
+    assert q["out_degree"]["max"] == 2 and q["out_degree"]["min"] == 0
+    assert q["out_degree"]["full_rows"] == 2 / 5
+    assert q["in_degree"]["max"] == 2 and q["in_degree"]["zero"] == 1 / 5
+    assert q["reachable_from_entry"] == 4 / 5
+    # edges 0-1, 0-2, 1-2, 2-3, 2-0, 3-0: reciprocal are 0->2 and 2->0
+    assert q["reciprocal_edges"] == 2 / 6
+    # exact 1-NN among out-neighbours: vertices 0, 1, 2, 3 yes, 4 no
+    assert q["exact_1nn_in_out_edges"] == 4 / 5
