@@ -61,7 +61,9 @@ def parse():
                     help="sift: the headline (default); the others measure the precision, batching and serving "
                          "workloads and print one JSON line each")
     ap.add_argument("--no-legs", action="store_true",
-                    help="skip the neighbour-grouping, precision and batching legs of the default run")
+                    help="skip the neighbour-grouping, precision, batching and 10M serving legs of the default run")
+    ap.add_argument("--serve-n", type=int, default=SERVE_N,
+                    help="point-set size of the serving workload (default 10M)")
     ap.add_argument("--kernel-digest", action="store_true",
                     help="print the digest of the CUDA sources that an ncu summary records, and exit")
     return ap.parse_args()
@@ -86,24 +88,33 @@ def recall_at_k(ids, gt):
     return hits / gt.size
 
 
-def exact_topk_gpu(base, queries, k, torch, metric="l2"):
+def exact_topk_gpu(base, queries, k, torch, metric="l2", block=1 << 21, qchunk=256):
     """Exact top-k by FP64 L2 (or -inner product) on the GPU with torch
-    (recall ground truth); ties broken by id."""
+    (recall ground truth), over blocks of base rows; ties broken by id."""
     dev = torch.device("cuda")
     X = torch.from_numpy(base).to(dev, torch.float64)
     xn = (X * X).sum(1)
+    n = X.shape[0]
     out = np.empty((queries.shape[0], k), np.int64)
-    for a in range(0, queries.shape[0], 1024):
-        Q = torch.from_numpy(queries[a:a + 1024]).to(dev, torch.float64)
-        if metric == "l2":
-            D = (Q * Q).sum(1, keepdim=True) + xn[None, :] - 2.0 * (Q @ X.T)
-        else:
-            D = -(Q @ X.T)
-        v, i = torch.topk(D, k + 8, dim=1, largest=False, sorted=True)
-        v, i = v.cpu().numpy(), i.cpu().numpy()
+    for a in range(0, queries.shape[0], qchunk):
+        Q = torch.from_numpy(queries[a:a + qchunk]).to(dev, torch.float64)
+        vs, ix = [], []
+        for c in range(0, n, block):
+            Xb = X[c:c + block]
+            if metric == "l2":
+                D = (Q * Q).sum(1, keepdim=True) + xn[None, c:c + block] - 2.0 * (Q @ Xb.T)
+            else:
+                D = -(Q @ Xb.T)
+            v, i = torch.topk(D, min(k + 8, Xb.shape[0]), dim=1, largest=False, sorted=True)
+            vs.append(v)
+            ix.append(i + c)
+            del D
+        v, i = torch.cat(vs, 1).cpu().numpy(), torch.cat(ix, 1).cpu().numpy()
         for r in range(v.shape[0]):
             o = np.lexsort((i[r], v[r]))
             out[a + r] = i[r][o][:k]
+    del X
+    torch.cuda.empty_cache()
     return out
 
 
@@ -492,7 +503,8 @@ def run_ours(args):
     }
     # the precision (1M x 960) and batching (100,000 uneven queries) workloads, short, as extra keys
     if not args.no_legs and world == 1:
-        for name, fn in (("gist_precision", gist_leg), ("deep_batch", deep_batch_leg)):
+        for name, fn in (("gist_precision", gist_leg), ("deep_batch", deep_batch_leg),
+                         ("serving_10m", lambda torch_, args_: serve_leg(torch_, n=args_.serve_n, nreq=10_000))):
             try:
                 t0 = time.time()
                 out[name] = fn(torch, args)
@@ -953,34 +965,74 @@ def run_deep_batch(args):
 
 # -------------------------------------------------------------- serving
 
-def run_serve(args):
-    """Continuous-batching server under Poisson arrivals: 1M x 96 BF16 unit
-    vectors (inner product), k in {10, 100}; latency percentiles at five
-    offered rates (0.1 .. 0.9 of the measured saturation rate)."""
+SERVE_N = 10_000_000
+
+
+def serve_graph(base, log_fn=None):
+    """The serving graph over the 10M point set: built on the GPU by the
+    library's builder (brute-force k-NN kernel, occlusion prune, reverse
+    fill, reachability repair), cached beside the synthetic point sets."""
+    from paper_2201_13007_gb300 import graph, synth
+    path = os.path.join(synth._cache_dir(), f"serve_graph_{base.shape[0]}_v1.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return z["adj"], int(z["entry"]), int(z["added"]), {"cached": True}
+    adj, entry, added, _, t = graph.build(base, R=32, k=64, cap=128, log=log_fn)
+    n = base.shape[0]
+    t["knn_pairs_per_s"] = n * (n - 1) / t["knn"]
+    t["knn_tflops"] = 2.0 * n * (n - 1) * base.shape[1] / t["knn"] / 1e12
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, adj=adj, entry=np.array(entry), added=np.array(added))
+    os.replace(tmp, path)
+    return adj, entry, added, t
+
+
+def serve_leg(torch, n=SERVE_N, nreq=20_000):
+    """Continuous-batching server under Poisson arrivals: n x 96 BF16 unit
+    vectors (inner product) on a GPU-built degree-32 graph, k in {10, 100},
+    recall targets 0.9 / 0.99 mapped to (L, M) on 2,000 calibration queries
+    and checked on 2,000 held-out ones; latency percentiles at five offered
+    rates (0.1 .. 0.9 of the measured saturation rate)."""
     import ctypes
     import threading as th
-    import torch
     from paper_2201_13007_gb300 import _abi, synth
     from paper_2201_13007_gb300.index import Index
-    w = synth.make_workload("deep", 1_000_000, 20_000, components=256)
-    ix = Index(w.base, w.adj, w.entry, storage="bf16", metric="ip")
-    gt = exact_topk_gpu(w.base, w.queries[:2000], 100, torch, metric="ip")
-    qd = torch.from_numpy(w.queries[:2000]).cuda()
-    pts = {}
+    t0 = time.time()
+    base, queries = synth.deep_bf16(n, 20_000)
+    data_s = time.time() - t0
+    t0 = time.time()
+    adj, entry, added, build_t = serve_graph(base, log)
+    graph_s = time.time() - t0
+    log(f"serving set {n} x {base.shape[1]} ready: data {data_s:.0f}s, graph {graph_s:.0f}s ({added} repair links)")
+    ix = Index(base, adj, entry, storage="bf16", metric="ip")
+    calib, held = queries[:2000], queries[2000:4000]
+    gt = exact_topk_gpu(base, np.concatenate([calib, held]), 100, torch, metric="ip")
+    gt_c, gt_h = gt[:2000], gt[2000:]
+    qd = torch.from_numpy(calib).cuda()
+    qh = torch.from_numpy(held).cuda()
+    hbm, _ = peaks()
+    pts, held_rec, cost = {}, {}, {}
     for kk in (10, 100):
         search = lambda qq, L, M: ix.search(qq, kk, L, M, persistent=True)[0]
-        pts[kk] = cheapest_points(torch, search, qd, gt[:, :kk], (100, 128, 160, 192, 256, 384, 512, 768, 1024),
+        pts[kk] = cheapest_points(torch, search, qd, gt_c[:, :kk], (100, 128, 160, 192, 256, 384, 512, 768, 1024),
                                   (8, 16), TARGETS, k=kk)
-    log("serving points", pts)
+        for tgt, (L, M, _) in pts[kk].items():
+            st = torch.empty((qh.shape[0], 8), dtype=torch.int64, device="cuda")
+            ids, _ = ix.search(qh, kk, L, M, persistent=True, stats=st)
+            held_rec[(kk, tgt)] = recall_at_k(ids.cpu().numpy()[:, :kk], gt_h[:, :kk])
+            sn = st.cpu().numpy()
+            cost[(kk, tgt)] = algorithmic_bytes(sn, ix.info()["R"], ix.info()["d_pad"] * 2, base.shape[1], kk,
+                                                0) / sn.shape[0]
+    log("serving points", pts, "held-out recall", held_rec)
     g = np.random.Generator(np.random.PCG64(5))
-    nreq = 20_000
     ks = g.choice([10, 100], nreq)
     tg = g.choice(TARGETS, nreq)
-    qi = g.integers(0, w.queries.shape[0], nreq)
+    qi = g.integers(4000, queries.shape[0], nreq)  # requests draw from queries outside both samples
     LL = np.array([pts[int(k_)][float(t_)][0] for k_, t_ in zip(ks, tg)], np.int32)
     MM = np.array([pts[int(k_)][float(t_)][1] for k_, t_ in zip(ks, tg)], np.int32)
+    bytes_per_req = float(np.mean([cost[(int(k_), float(t_))] for k_, t_ in zip(ks, tg)]))
     cfg = _abi.ServeConfig(max_batch=512, streams=4, max_k=100, max_L=int(LL.max()), max_M=16)
-    res_all = []
 
     def run(rate):
         srv = ctypes.c_void_p(_abi.ann_serve_create(ix.handle, cfg))
@@ -1004,7 +1056,7 @@ def run_serve(args):
         for i in range(nreq):
             while rate and time.perf_counter() - t0 < arr[i]:
                 pass
-            qv = w.queries[qi[i]]
+            qv = queries[qi[i]]
             while _abi.ann_serve_submit(srv, ctypes.c_void_p(qv.ctypes.data), int(ks[i]), int(LL[i]), int(MM[i]), i) \
                     == _abi.ANN_ERR_BUSY:
                 busy += 1
@@ -1019,17 +1071,32 @@ def run_serve(args):
                 "device_p99_us": float(np.percentile(dev, 99)), "busy_retries": busy}
 
     sat = run(0)  # flood: every request submitted as fast as the client can
+    sat["hbm_gbs"] = sat["achieved_qps"] * bytes_per_req / 1e9
+    sat["hbm_frac"] = sat["hbm_gbs"] / hbm
     log("saturation", sat)
+    rates = []
     for f in (0.1, 0.3, 0.5, 0.7, 0.9):
         r = run(f * sat["achieved_qps"])
-        res_all.append(r)
+        rates.append(r)
         log(f, r)
-    out = {"workload": "deep-like 1M x 96 BF16 unit vectors (inner product), 256 components, k in {10,100}, "
-                       "recall targets 0.9/0.99 mapped to L; Poisson arrivals",
-           "points": {str(k_): {str(t_): v for t_, v in d.items()} for k_, d in pts.items()},
-           "saturation": sat, "rates": res_all,
-           "client": "one Python thread submitting through ctypes, one polling"}
-    print(json.dumps(out))
+    ix.close()
+    return {"workload": f"deep-like {n} x 96 BF16 unit vectors (inner product), 256 components, degree-32 graph "
+                        f"built on the GPU (brute-force k-NN kernel, k=64); k in {{10,100}}, recall targets "
+                        f"0.9/0.99 mapped to (L, M); Poisson arrivals; {nreq} requests per rate",
+            "points": {str(k_): {str(t_): {"L": v[0], "M": v[1], "recall_calibration": v[2],
+                                           "recall_held_out": held_rec[(k_, t_)],
+                                           "algorithmic_bytes_per_query": cost[(k_, t_)]}
+                                 for t_, v in d.items()} for k_, d in pts.items()},
+            "saturation": sat, "rates": rates, "graph_build_s": build_t, "data_s": data_s,
+            "repair_links": added,
+            "hbm": "saturation QPS x mean algorithmic bytes per request (adjacency rows of expanded vertices + "
+                   "one BF16 row per distance, counted on the held-out sample) / measured copy bandwidth",
+            "client": "one Python thread submitting through ctypes, one polling"}
+
+
+def run_serve(args):
+    import torch
+    print(json.dumps(serve_leg(torch, n=args.serve_n)))
 
 
 def main():

@@ -223,6 +223,29 @@ int ann_index_get_info(const ann_index *index, ann_index_info *info);
  * ANN_ERR_OOM, ANN_ERR_CUDA. */
 int ann_index_group_neighbors(ann_index *index, float hot_fraction, int32_t prefetch);
 
+/* Exact k nearest base rows of every query row by a brute-force scan
+ * (Def. 1 of Sec. 2.1 over BF16 data), for building the similarity graph
+ * the search runs on; the paper assumes the graph exists (Sec. 2.2), and its
+ * k-NN candidate lists are these neighbours. The n x nq distance matrix is
+ * never stored: tensor-core tiles of it are filtered into per-row top-64
+ * lists in shared memory.
+ *   base       device, n x d BF16 bit patterns, row-major, 16-byte aligned.
+ *   queries    device, nq x d BF16 bit patterns, row-major, 16-byte aligned
+ *              (may be a slice of base).
+ *   d          32, 64, 96 or 128.
+ *   self_offset -1, or the base row of query 0: query i is then base row
+ *              self_offset + i and is left out of its own result.
+ *   metric     ann_metric; keys are squared l2 or -<q, x>, products exact
+ *              in FP32 and sums in FP32.
+ *   k          1..64 results per query.
+ *   out_ids    device int32 nq x k, out_dists device float nq x k, ascending
+ *              by (key, id); slots beyond the available rows hold (-1, +inf).
+ * Synchronous (the call waits for stream). Errors: ANN_ERR_ARG (shape,
+ * alignment, range), ANN_ERR_OOM, ANN_ERR_CUDA. Work: n * nq * d
+ * multiply-adds on the tensor cores, plus 256 threads per 128 queries. */
+int ann_knn_bf16(const void *base, int64_t n, int32_t d, const void *queries, int64_t nq, int64_t self_offset,
+                 int32_t metric, int32_t k, int32_t *out_ids, float *out_dists, void *stream);
+
 /* Search nq queries (Algorithm 1 / Sec. 4.1-4.2 top-M with M doubling from 1,
  * one CTA per query).
  *   queries    device, nq x d float32 row-major.

@@ -9,6 +9,8 @@ The arithmetic lives in ``oracle.c`` (plain C, FP64); this module compiles it
 with gcc and marshals numpy arrays through ctypes. Function-to-passage map:
 
 - :func:`exact_knn`  -- Def. 1 (K-NNS), Sec. 2.1, brute force.
+- :func:`exact_knn_gemm`, :func:`exact_knn_blocked` -- Def. 1 through FP64
+  matrix products (whole, or by blocks of base rows for 10M-point sets).
 - :func:`search` with ``algo="bfis"``  -- Algorithm 1 (BFiS).
 - :func:`search` with ``algo="topm"``  -- Sec. 4.1 top-M parallel neighbour
   expansion (BSP) with the Sec. 4.2 staged schedule.
@@ -246,6 +248,58 @@ def exact_knn_gemm(base, queries, K, metric="l2", chunk=256):
         if kk < K:
             ids[a:a + chunk, kk:] = -1
             keys[a:a + chunk, kk:] = np.inf
+    return ids, keys
+
+
+def exact_knn_blocked(base, queries, K, metric="l2", block=1 << 20, qchunk=256):
+    """Def. 1 over base sets too large for one distance matrix, in plain
+    PyTorch CPU ops (FP64): the keys of exact_knn_gemm, formed block by
+    block of ``block`` base rows. Within a block, every id whose key is at
+    most the block's K-th smallest key becomes a candidate, so ids tied at a
+    block's cut all take part; the answer is the K smallest candidates by
+    (key, id). The library matrix product and top-k selection serve as steps.
+    Returns (ids int64 nq x K, keys float64 nq x K), padded with (-1, +inf)."""
+    import torch
+    Q = torch.from_numpy(np.ascontiguousarray(queries, np.float64))
+    if Q.ndim == 1:
+        Q = Q[None, :]
+    nq = Q.shape[0]
+    n = base.shape[0]
+    qn = (Q * Q).sum(1)
+    cand_i = [[] for _ in range(nq)]
+    cand_k = [[] for _ in range(nq)]
+    for a in range(0, n, block):
+        Xb = torch.from_numpy(np.ascontiguousarray(base[a:a + block], np.float64))
+        xn = (Xb * Xb).sum(1)
+        kk = min(K, Xb.shape[0])
+        for c in range(0, nq, qchunk):
+            q = Q[c:c + qchunk]
+            if metric == "l2":
+                # |x|^2 - 2<q, x> in one product; |q|^2 is added to the selected keys
+                # only (the same two roundings as |x|^2 - 2<q, x> + |q|^2)
+                D = torch.addmm(xn[None, :].expand(q.shape[0], -1), q, Xb.T, beta=1.0, alpha=-2.0)
+            else:
+                D = torch.mm(q, Xb.T).neg_()
+            kth = torch.topk(D, kk, dim=1, largest=False, sorted=True).values[:, -1]
+            rows, cols = torch.nonzero(D <= kth[:, None], as_tuple=True)
+            vals = D[rows, cols]
+            if metric == "l2":
+                vals = vals + qn[c:c + qchunk][rows]
+            vals = vals.numpy()
+            rows, cols = rows.numpy(), cols.numpy()
+            for r in np.unique(rows):
+                m = rows == r
+                cand_i[c + r].append(cols[m].astype(np.int64) + a)
+                cand_k[c + r].append(vals[m])
+            del D
+    ids = np.full((nq, K), -1, np.int64)
+    keys = np.full((nq, K), np.inf)
+    for r in range(nq):
+        ci = np.concatenate(cand_i[r])
+        ck = np.concatenate(cand_k[r])
+        o = np.lexsort((ci, ck))[:K]
+        ids[r, :o.size] = ci[o]
+        keys[r, :o.size] = ck[o]
     return ids, keys
 
 

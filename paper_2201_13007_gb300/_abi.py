@@ -99,6 +99,7 @@ def lib():
             L.ann_index_destroy.restype = None
             L.ann_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
             L.ann_index_group_neighbors.argtypes = [vp, ctypes.c_float, i32]
+            L.ann_knn_bf16.argtypes = [vp, i64, i32, vp, i64, i64, i32, i32, vp, vp, vp]
             L.ann_search.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
             L.ann_search_ex.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
             L.ann_search_host.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(SearchParams), vp]
@@ -150,6 +151,10 @@ def ann_index_get_info(index) -> IndexInfo:
 
 def ann_index_group_neighbors(index, hot_fraction, prefetch) -> None:
     _check(lib().ann_index_group_neighbors(index, float(hot_fraction), int(prefetch)))
+
+
+def ann_knn_bf16(base, n, d, queries, nq, self_offset, metric, k, out_ids, out_dists, stream) -> None:
+    _check(lib().ann_knn_bf16(base, n, d, queries, nq, self_offset, metric, k, out_ids, out_dists, stream))
 
 
 def ann_search(index, queries, nq, k, L, M, out_ids, out_dists, stream) -> None:

@@ -486,6 +486,38 @@ int ann_index_get_info(const ann_index *index, ann_index_info *info) {
     return ANN_OK;
 }
 
+int ann_knn_bf16(const void *base, int64_t n, int32_t d, const void *queries, int64_t nq, int64_t self_offset,
+                 int32_t metric, int32_t k, int32_t *out_ids, float *out_dists, void *stream) {
+    if (!base || !queries || !out_ids || !out_dists) return fail(ANN_ERR_ARG, "null pointer");
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(ANN_ERR_ARG, "n=%lld outside [1, 2^31)", (long long)n);
+    if (nq < 0 || nq >= (int64_t(1) << 31)) return fail(ANN_ERR_ARG, "nq=%lld outside [0, 2^31)", (long long)nq);
+    if (d != 32 && d != 64 && d != 96 && d != 128) return fail(ANN_ERR_ARG, "d=%d not in {32, 64, 96, 128}", d);
+    if (k < 1 || k > 64) return fail(ANN_ERR_ARG, "k=%d outside [1, 64]", k);
+    if (metric != ANN_METRIC_L2 && metric != ANN_METRIC_IP) return fail(ANN_ERR_ARG, "metric=%d", metric);
+    if (((uintptr_t)base & 15) || ((uintptr_t)queries & 15))
+        return fail(ANN_ERR_ARG, "base and queries must be 16-byte aligned");
+    if (self_offset < -1 || (self_offset >= 0 && self_offset + nq > n))
+        return fail(ANN_ERR_ARG, "self_offset=%lld does not place the queries inside the base", (long long)self_offset);
+    if (nq == 0) return ANN_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float *norms = nullptr;
+    int *err = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&norms, (size_t)ann::knn_norms_rows(n) * 4 + 16)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(knn norms)");
+    err = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(norms) + (size_t)ann::knn_norms_rows(n) * 4);
+    int herr = 0;
+    if ((e = cudaMemsetAsync(err, 0, 4, s)) == cudaSuccess &&
+        (e = ann::launch_knn_bf16(base, n, d, queries, nq, self_offset, metric, k, out_ids, out_dists, norms, err,
+                                  s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(norms);
+    if (e != cudaSuccess) return cuda_fail(e, "knn");
+    if (herr) return fail(ANN_ERR_CUDA, "knn: a candidate merge did not converge");
+    return ANN_OK;
+}
+
 int ann_index_group_neighbors(ann_index *index, float hot_fraction, int32_t prefetch) {
     if (!index) return fail(ANN_ERR_ARG, "index is NULL");
     if (!(hot_fraction >= 0.f && hot_fraction <= 0.05f))

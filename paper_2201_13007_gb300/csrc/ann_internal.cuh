@@ -174,6 +174,14 @@ cudaError_t launch_encode(const float *src, int64_t n, int32_t d, int storage, v
 cudaError_t launch_count_bad_adj(const int32_t *adj, int64_t count, int64_t n, unsigned long long *bad,
                                  cudaStream_t stream);
 cudaError_t launch_count_in_degree(const int32_t *adj, int64_t count, int32_t *deg, cudaStream_t stream);
+
+// knn.cu: brute-force k-NN over BF16 rows (graph construction). norms holds
+// knn_norms_rows(n) floats for l2 (unused for inner product); err is a
+// device int set to 1 if a CTA's merge rounds ran out.
+int64_t knn_norms_rows(int64_t n);
+cudaError_t launch_knn_bf16(const void *base, int64_t n, int d, const void *queries, int64_t nq, int64_t self0,
+                            int metric, int k, int32_t *ids, float *dists, float *norms, int *err,
+                            cudaStream_t stream);
 cudaError_t launch_fill_groups(unsigned char *rows, float *scales, const int32_t *adj, const int32_t *hot,
                                int64_t n_hot, int32_t R, int64_t n, int32_t row_bytes, cudaStream_t stream);
 

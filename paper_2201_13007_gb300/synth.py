@@ -324,21 +324,22 @@ def _nearest_among(x, targets, pool, device=None):
 
 
 def repair_reachability(adj: np.ndarray, entry: int, knn: np.ndarray, x: np.ndarray,
-                        max_rounds: int = 256, per_round: int = 1024, device=None):
+                        max_rounds: int = 256, per_round: int = 1024, device=None, reach=None):
     """Make every vertex reachable from ``entry``. Each round finds the
     unreachable set by BFS and links up to ``per_round`` of its vertices
     (evenly spaced by id) from their nearest reachable vertex that still has
     room (a free slot, else one of its last slots; at most R/2 slots of a row
     are given to such links); a link makes the whole part of the graph behind
     that vertex reachable. ``device`` forces the torch device of the
-    nearest-vertex search ("cpu" keeps the repair off the GPU). Returns (adj,
-    number of links added)."""
+    nearest-vertex search ("cpu" keeps the repair off the GPU); ``reach``
+    replaces the BFS (same contract as reachable_from). Returns (adj, number
+    of links added)."""
     adj = adj.copy()
     n, R = adj.shape
     protected = np.zeros((n, R), bool)
     added = 0
     for _ in range(max_rounds):
-        mask = reachable_from(adj, entry)
+        mask = (reach or reachable_from)(adj, entry)
         un = np.flatnonzero(~mask)
         if un.size == 0:
             return adj, added
@@ -470,6 +471,27 @@ def make_workload(kind: str, n: int, nq: int, *, d: int | None = None, R: int | 
     return Workload(name=kind, base=z["base"], queries=z["queries"], adj=z["adj"],
                     entry=int(z["entry"]), metric=metric,
                     meta={"repaired_links": int(z["repaired"]), **spec})
+
+
+def deep_bf16(n: int, nq: int, components: int = 256, cache: bool = True):
+    """The serving point set: mixture_deep unit vectors (``components``
+    mixture components) rounded to BF16, so that BF16 storage holds them
+    exactly; queries stay FP32. No graph: large sets get theirs from the
+    library's GPU builder. Returns (base n x d float32, queries nq x d
+    float32)."""
+    import torch
+    spec = {"kind": "deep_bf16", "n": n, "nq": nq, "components": components, "v": 1}
+
+    def gen():
+        base, q = mixture_deep(n, nq, C=components)
+        step = 1 << 20
+        for a in range(0, n, step):
+            blk = torch.from_numpy(base[a:a + step])
+            base[a:a + step] = blk.to(torch.bfloat16).to(torch.float32).numpy()
+        return {"base": base, "queries": q}
+
+    z = _load_or_build(spec, gen) if cache else gen()
+    return z["base"], z["queries"]
 
 
 def graph_quality(adj: np.ndarray, entry: int, knn: np.ndarray | None = None, sample: int = 2000,

@@ -123,6 +123,40 @@ def test_exact_knn_gemm_float_data_within_fp64_rounding(oracle_mod):
     np.testing.assert_allclose(gk, keys, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_exact_knn_blocked_equals_the_plain_sum_on_integer_data(oracle_mod, metric):
+    """The block-by-block form of Def. 1 on integer data (exact keys) equals
+    the plain per-coordinate sum bit for bit, with blocks small enough that
+    runs of tied keys straddle block cuts, query chunks that do not divide
+    the query count, and a last block shorter than K."""
+    r = np.random.default_rng(16)
+    base = r.integers(0, 256, (1003, 96)).astype(np.float32)
+    base[500:560] = base[10:70]                      # ties across blocks
+    base[990:1003] = base[0]                         # a run of 13 equal rows, one split by a cut
+    q = r.integers(0, 256, (23, 96)).astype(np.float32)
+    q[2] = base[15]
+    q[4] = base[0]
+    ids, keys = oracle_mod.exact_knn(base, q, 20, metric=metric, nthreads=4)
+    gi, gk = oracle_mod.exact_knn_blocked(base, q, 20, metric=metric, block=97, qchunk=5)
+    np.testing.assert_array_equal(gi, ids)
+    np.testing.assert_array_equal(gk, keys)
+
+
+def test_exact_knn_blocked_float_data_and_padding(oracle_mod):
+    r = np.random.default_rng(17)
+    base = r.standard_normal((1500, 32)).astype(np.float32)
+    q = r.standard_normal((9, 32)).astype(np.float32)
+    ids, keys = oracle_mod.exact_knn(base, q, 12)
+    gi, gk = oracle_mod.exact_knn_blocked(base, q, 12, block=256)
+    np.testing.assert_array_equal(gi, ids)
+    np.testing.assert_allclose(gk, keys, rtol=1e-12, atol=1e-12)
+    small = base[:5]
+    gi, gk = oracle_mod.exact_knn_blocked(small, q[:2], 8, block=2)
+    ids, keys = oracle_mod.exact_knn(small, q[:2], 8)
+    np.testing.assert_array_equal(gi, ids)
+    assert np.isinf(gk[:, 5:]).all()
+
+
 def test_exact_knn_pads_when_k_exceeds_n(oracle_mod):
     base = np.arange(3, dtype=np.float32).reshape(3, 1)
     ids, keys = oracle_mod.exact_knn(base, np.array([[0.2]], np.float32), 5)
