@@ -126,12 +126,15 @@ typedef struct {
      * shared memory (lower latency per query); 0 or 1 = one CTA per query.
      * A clustered search is never persistent (one cluster per query). */
     int32_t cluster;
-    /* Sync one-CTA kernel only: device int64 array of nq x 4, or NULL. When
-     * given, each query's SM clock cycles spent in its step phases are
-     * written there: [0] select (first M unchecked), [1] expand (adjacency
-     * rows + visited table), [2] distance gather, [3] sort + dedupe + merge.
-     * These are the Expand / Merge / Seq parts of the paper's time
-     * breakdown (Fig. 14). */
+    /* Sync kernels only: device int64 array of nq x 4, or NULL. When given,
+     * each query's SM clock cycles spent in its step phases are written
+     * there. One-CTA kernel: [0] select (first M unchecked), [1] expand
+     * (adjacency rows + visited table), [2] distance gather, [3] sort +
+     * dedupe + merge. Cluster kernel (cycles of the cluster's first CTA):
+     * [0] select, [1] expand + distance of its own vertices, [2] exchange
+     * (cluster barrier and the copy of every CTA's survivors), [3] sort +
+     * dedupe + merge. These are the Expand / Merge / Seq parts of the
+     * paper's time breakdown (Fig. 14). */
     int64_t *phase_cycles;
     /* Visited set: 1 = open-addressing table of ids, exact until it is half
      * full, then reset to the queued ids; 2 = direct-mapped cache that

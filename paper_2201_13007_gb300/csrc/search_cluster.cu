@@ -31,6 +31,7 @@ struct ClusterCtrl {
     int unsafe, anydup, first_un, sel_found, sel_last, wevals;
     int rr_n;          // re-rank keys appended (rank 0, after the search; never read by another CTA)
     long long steps, expansions, dropped, t0;
+    long long ph[4], tmark;  // rank 0's phase cycles (select, expand + distance, exchange, sort + merge)
 };
 
 // Segments: query, two queue buffers, per-warp fresh lists (then sort
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
         ctl.unsafe = 0;
         ctl.first_un = 0;
         ctl.wevals = 0;
+        ctl.ph[0] = ctl.ph[1] = ctl.ph[2] = ctl.ph[3] = 0;
     }
     const float *qg = a.queries + (size_t)qi * a.d;
     for (int i = tid; i < a.qfloats; i += NT) qv[i] = i < a.d ? qg[i] : 0.f;
@@ -139,6 +141,14 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     int Mcur = a.M0 < Mmax ? a.M0 : Mmax;
     int step = 0;
     int qlen = 1;
+    const bool prof = a.phase_cycles != nullptr && rank == 0;
+    if (prof && tid == 0) ctl.tmark = clock64();
+#define ANN_CPHASE(i)                                  \
+    if (prof && tid == 0) {                            \
+        const long long now_ = clock64();              \
+        ctl.ph[i] += now_ - ctl.tmark;                 \
+        ctl.tmark = now_;                              \
+    }
     for (;;) {
         const int par = step & 1;
         // --- select (every CTA, identical): warp 0 takes the first Mcur unchecked entries
@@ -165,6 +175,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
             }
         }
         __syncthreads();
+        ANN_CPHASE(0)
         const int found = ctl.sel_found;
         const int nact = found < Mcur ? found : Mcur;
         if (nact == 0) break;  // identical in every CTA: all leave the loop at the same step
@@ -181,15 +192,31 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
                                              &ctl.pub_n[par]);
         __syncthreads();
         if (tid == 0) ctl.pub_unsafe[par] = ctl.unsafe;
+        ANN_CPHASE(1)
         cluster.sync();  // every CTA's survivors of this step are published
-        // gather the union in rank order (the same order in every CTA)
+        // gather the union in rank order (the same order in every CTA): every thread reads all
+        // counts at once, then copies its share of all lists in one pass (two remote round trips)
+        int cn[8];
         int tot = 0, any_unsafe = 0;
-        for (int r = 0; r < C; ++r) {
-            const int n = *cluster.map_shared_rank(&ctl.pub_n[par], r);
-            const entry_t *rp = cluster.map_shared_rank(pub[par], r);
-            for (int i = tid; i < n; i += NT) uni[tot + i] = rp[i];
-            tot += n;
-            any_unsafe |= *cluster.map_shared_rank(&ctl.pub_unsafe[par], r);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            cn[r] = 0;
+            if (r < C) {
+                cn[r] = *cluster.map_shared_rank(&ctl.pub_n[par], r);
+                any_unsafe |= *cluster.map_shared_rank(&ctl.pub_unsafe[par], r);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) tot += cn[r];
+        for (int i = tid; i < tot; i += NT) {
+            int r = 0, base_r = 0;
+#pragma unroll
+            for (int rr = 0; rr < 7; ++rr)
+                if (r == rr && i - base_r >= cn[rr]) {
+                    base_r += cn[rr];
+                    r = rr + 1;
+                }
+            uni[i] = cluster.map_shared_rank(pub[par], r)[i - base_r];
         }
         if (tid < nact) Q[sel_pos[tid]] |= kChecked;  // the selection is taken: mark it
         if (tid == 0) {
@@ -199,6 +226,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
             ctl.first_un = ctl.sel_last + 1;
         }
         __syncthreads();
+        ANN_CPHASE(2)
         if (tot > 0) {
             const int ncl = sort_dedupe_merge<NT>(Q, qlen, uni, tot, cand, Qn, L, any_unsafe != 0, dup, &ctl.anydup,
                                                   &ctl.dropped, &ctl.first_un);
@@ -209,8 +237,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
         } else {
             __syncthreads();
         }
+        ANN_CPHASE(3)
         if (step % a.t == 0) Mcur = min(2 * Mcur, Mmax);
     }
+#undef ANN_CPHASE
 
     // distance evaluations of the whole cluster: every CTA's own fresh vertices (read before the last barrier)
     long long evals = 1;
@@ -266,6 +296,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
             st.t_end_ns = global_ns();
             a.stats[qi] = st;
         }
+        if (tid == 0 && prof)
+            for (int i = 0; i < 4; ++i) a.phase_cycles[(size_t)qi * 4 + i] = ctl.ph[i];
     }
     cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
