@@ -1,5 +1,6 @@
 // ann_api.cu -- host side of the C ABI declared in include/ann.h: argument
 // checks, index memory, kernel selection and launch.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -59,19 +60,32 @@ void free_index_data(ann::IndexData &x) {
     x = ann::IndexData();
 }
 
-int sm_count() {
-    int dev = 0, sms = 0;
+// Device properties that a search plan reads, cached per device.
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_sms[kMaxDevices], g_smem_optin[kMaxDevices];
+
+int device_attr(std::atomic<int> *cache, cudaDeviceAttr attr) {
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev < 0 || dev >= kMaxDevices) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, attr, dev);
+        return v;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        cudaDeviceGetAttribute(&v, attr, dev);
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+int sm_count() {
+    const int sms = device_attr(g_sms, cudaDevAttrMultiProcessorCount);
     return sms > 0 ? sms : 1;
 }
 
-int max_dyn_smem() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
-}
+int max_dyn_smem() { return device_attr(g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin); }
 
 int create_impl(const float *base, int64_t n, int32_t d, int32_t storage, const int32_t *adj, int32_t R,
                 int64_t entry, int32_t metric, int32_t flags, ann_index **out) {
@@ -455,6 +469,21 @@ int launch_plan(const ann_index *index, const Plan &plan_in, cudaStream_t s) {
 
 namespace ann {
 void set_error(const char *msg) { g_err = msg; }
+
+cudaError_t ensure_dyn_smem(const void *kernel, int smem) {
+    static std::mutex mu;
+    static std::unordered_map<std::string, int> limit;  // (kernel, device) -> the limit set so far
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::string key = std::to_string(reinterpret_cast<uintptr_t>(kernel)) + "/" + std::to_string(dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = limit.find(key);
+    if (it != limit.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) limit[key] = smem;
+    return e;
+}
 }  // namespace ann
 
 extern "C" {

@@ -148,6 +148,11 @@ int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits);
 // ann_api.cu: sets the calling thread's ann_last_error() text
 void set_error(const char *msg);
 
+// ann_api.cu: raise a kernel's dynamic shared-memory limit to at least smem
+// bytes on the current device; the attribute is set only when a launch needs
+// more than any earlier one (the call costs microseconds on a latency path).
+cudaError_t ensure_dyn_smem(const void *kernel, int smem);
+
 // ann_api.cu: argument checks and launch configuration of one search
 struct Plan {
     SearchArgs a;

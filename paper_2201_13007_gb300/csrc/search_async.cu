@@ -372,7 +372,7 @@ int async_smem_size(int qfloats, int Lcap, int walkers, int hash_bits) {
 template <int NT, int STORE>
 static cudaError_t alaunch_t(const SearchArgs &a, int smem, int grid, cudaStream_t s) {
     auto fn = async_search_kernel<NT, STORE>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
@@ -381,7 +381,7 @@ static cudaError_t alaunch_t(const SearchArgs &a, int smem, int grid, cudaStream
 template <int NT, int STORE>
 static cudaError_t aocc_t(int smem, int *bps) {
     auto fn = async_search_kernel<NT, STORE>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, NT, smem);
 }

@@ -28,7 +28,8 @@ struct ClusterCtrl {
     int pub_n[2];      // survivors published in the step of this parity
     int pub_fresh[2];  // fresh vertices of this CTA in the step of this parity
     int pub_unsafe[2]; // this CTA's visited set may have forgotten a vertex (as of this step)
-    int unsafe, anydup, first_un, sel_found, sel_last, wevals;
+    int unsafe, anydup, first_un, sel_last, wevals;
+    int wcnt[32];      // per-warp counts of the selection scan
     int rr_n;          // re-rank keys appended (rank 0, after the search; never read by another CTA)
     long long steps, expansions, dropped, t0;
     long long ph[4], tmark;  // rank 0's phase cycles (select, expand + distance, exchange, sort + merge)
@@ -82,7 +83,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     const int slots_w = (a.M * R + NW - 1) / NW;
     uint2 *fresh = reinterpret_cast<uint2 *>(cand) + (size_t)warp * slots_w;
     const uint32_t r_recip = 0xFFFFFFFFu / (uint32_t)R + 1u;
-    const unsigned lt_mask = (1u << lane) - 1u;
 
     // one query per cluster; identical in every CTA of the cluster
     const int item = (int)(blockIdx.x / C);
@@ -151,32 +151,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     }
     for (;;) {
         const int par = step & 1;
-        // --- select (every CTA, identical): warp 0 takes the first Mcur unchecked entries
-        if (warp == 0) {
-            int found = 0, last_pos = -1;
-            for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
-                const int i = b + lane;
-                const entry_t e = i < qlen ? Q[i] : kChecked;
-                const bool un = !(e & kChecked);
-                const unsigned bal = __ballot_sync(kFull, un);
-                const int r = found + __popc(bal & lt_mask);
-                const bool take = un && r < Mcur;
-                if (take) {
-                    sel_id[r] = (int)entry_id(e);
-                    sel_pos[r] = i;
-                }
-                const unsigned tb = __ballot_sync(kFull, take);
-                if (tb) last_pos = b + 31 - __clz(tb);
-                found += __popc(bal);
-            }
-            if (lane == 0) {
-                ctl.sel_found = found;
-                ctl.sel_last = last_pos;
-            }
-        }
-        __syncthreads();
+        // --- select (every CTA, identical): the first Mcur unchecked entries, all warps scanning
+        const int found = select_unchecked<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
+                                               &ctl.sel_last);
         ANN_CPHASE(0)
-        const int found = ctl.sel_found;
         const int nact = found < Mcur ? found : Mcur;
         if (nact == 0) break;  // identical in every CTA: all leave the loop at the same step
         step++;
@@ -310,7 +288,7 @@ int cluster_smem_size(int qfloats, int Lcap, int Ccap, int hash_bits, int Mcap) 
 template <int NT, int STORE>
 static cudaError_t claunch_t(const SearchArgs &a, int smem, int csize, cudaStream_t s) {
     auto fn = a.metric == ANN_METRIC_L2 ? cluster_search_kernel<NT, STORE, true> : cluster_search_kernel<NT, STORE, false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.nq * csize));

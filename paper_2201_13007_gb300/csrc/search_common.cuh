@@ -852,6 +852,51 @@ __device__ __forceinline__ int visit_set(uint32_t *table, const SearchArgs &a, u
 // of a neighbour grouping gives its neighbours' rows in its group block
 // (one bulk prefetch for the block). Sets *unsafe if an insert may have
 // forgotten another vertex. Returns the fresh vertices this warp found.
+// The step's selection (Sec. 4.1, top-M): the first Mcur unchecked entries
+// of the stable queue Q[0, qlen) in queue order, taken into sel_id / sel_pos
+// by rank. The scan starts at first_un (every entry before it is checked)
+// and covers NW * 32 entries per round, one 32-entry chunk per warp; a block
+// scan of the warps' counts gives each chunk its first rank. Returns, in
+// every thread, the number of unchecked entries seen (at least the number
+// taken); *sel_last gets the queue position of the last entry taken (-1 if
+// none). wcnt is NW ints of shared memory. Every thread of the block must
+// call it; when the scan ran, it ends with a barrier.
+template <int NW>
+__device__ __forceinline__ int select_unchecked(const entry_t *Q, int qlen, int first_un, int Mcur, int *sel_id,
+                                                int *sel_pos, int *wcnt, int *sel_last) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (threadIdx.x == 0) *sel_last = -1;
+    int found = 0;
+    for (int base = first_un & ~31; found < Mcur && base < qlen; base += NW * 32) {
+        const int i = base + warp * 32 + lane;
+        const entry_t e = i < qlen ? Q[i] : kChecked;
+        const bool un = !(e & kChecked);
+        const unsigned bal = __ballot_sync(kFull, un);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int c = lane < NW ? wcnt[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < NW; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, c, o);
+            if (lane >= o) c += v;
+        }
+        const int total = __shfl_sync(kFull, c, NW - 1);
+        const int pre = warp > 0 ? __shfl_sync(kFull, c, warp - 1) : 0;
+        const int r = found + pre + __popc(bal & lt_mask);
+        const bool take = un && r < Mcur;
+        if (take) {
+            sel_id[r] = (int)entry_id(e);
+            sel_pos[r] = i;
+        }
+        const unsigned tb = __ballot_sync(kFull, take);
+        if (tb && lane == 0) atomicMax(sel_last, base + warp * 32 + 31 - __clz(tb));
+        found += total;
+        __syncthreads();
+    }
+    return found;
+}
+
 template <int NW>
 __device__ __forceinline__ int expand_step(const SearchArgs &a, uint32_t *table, const int *sel_id, int nact,
                                            uint32_t r_recip, uint32_t row_bytes, uint2 *fresh, uint2 *block,

@@ -46,7 +46,8 @@ struct Ctrl {
     int first_un;  // every queue entry before this position is checked
     int qi, k, L, Mmax;  // the query and its settings (kept here, not in registers, across the step loop)
     int wevals;    // fresh vertices of this query, summed per warp and step
-    int sel_found, sel_last;  // the step's selection: unchecked entries seen, position of the last taken
+    int sel_last;             // the step's selection: queue position of the last entry taken
+    int wcnt[32];             // per-warp counts of the selection scan
     // per-query counters, updated by thread 0 only
     long long steps, expansions, evals, resets, dropped, t0;
     long long ph[4], tmark;  // phase cycles (select, expand, distance, sort+merge) when requested
@@ -59,7 +60,6 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Ctrl ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const uint32_t row_bytes = (uint32_t)a.d_pad * ES;
     const uint32_t cpr = row_bytes / 16u;
     const SmemLayout &lay = a.sync_lay;
@@ -176,33 +176,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 __syncthreads();
             }
             const int par = step & 1;
-            // --- select: warp 0 takes the first Mcur unchecked entries (rank order) of the stable queue
-            // (entries before first_un are all checked)
-            int found = 0, last_pos = -1;
-            if (warp == 0) {
-                for (int b = ctl.first_un & ~31; b < qlen && found < Mcur; b += 32) {
-                    const int i = b + lane;
-                    const entry_t e = i < qlen ? Q[i] : kChecked;
-                    const bool un = !(e & kChecked);
-                    const unsigned bal = __ballot_sync(kFull, un);
-                    const int r = found + __popc(bal & lt_mask);
-                    const bool take = un && r < Mcur;
-                    if (take) {
-                        sel_id[r] = (int)entry_id(e);
-                        sel_pos[r] = i;
-                    }
-                    const unsigned tb = __ballot_sync(kFull, take);
-                    if (tb) last_pos = b + 31 - __clz(tb);
-                    found += __popc(bal);
-                }
-                if (lane == 0) {
-                    ctl.sel_found = found;
-                    ctl.sel_last = last_pos;
-                }
-            }
-            __syncthreads();
-            found = ctl.sel_found;
-            last_pos = ctl.sel_last;
+            // --- select: the first Mcur unchecked entries (rank order) of the stable queue, all warps
+            // scanning from first_un (entries before it are all checked)
+            const int found = select_unchecked<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
+                                                   &ctl.sel_last);
             const int nact = found < Mcur ? found : Mcur;
             if (nact == 0) break;  // no unchecked vertex left (identical in every warp)
             ANN_PHASE(0)
@@ -252,7 +229,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
                 ctl.nfresh[par ^ 1] = 0;
                 ctl.steps++;
                 ctl.expansions += nact;
-                ctl.first_un = last_pos + 1;
+                ctl.first_un = ctl.sel_last + 1;
                 ctl.do_reset = a.visited_mode == 0 && ctl.hash_count * 2 > H;
             }
             if (ns > 0) {
@@ -342,7 +319,7 @@ static auto sync_kernel_for(int metric) {
 template <int STORE>
 cudaError_t launch_sync_store(const SearchArgs &a, int threads, int smem, int grid, cudaStream_t s) {
     auto go = [&](auto fn) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
         if (e != cudaSuccess) return e;
         switch (threads) {
             case 64: fn<<<grid, 64, smem, s>>>(a); break;
@@ -364,7 +341,7 @@ cudaError_t launch_sync_store(const SearchArgs &a, int threads, int smem, int gr
 template <int STORE>
 cudaError_t occupancy_sync_store(int metric, int threads, int smem, int *bps) {
     auto occ = [&](auto fn, int nt) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(fn), smem);
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, nt, smem);
     };
