@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 K = 10
 TARGETS = (0.9, 0.99)
 CALIB = 2000  # queries the operating points are chosen on; recall is also reported on the others
-L_SWEEP = (10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024,
+L_SWEEP = (10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 448, 512, 576, 640, 704, 768, 896, 1024,
            1280, 1536, 2048)
 M_SWEEP = (4, 8, 16, 32)
 
@@ -398,35 +398,8 @@ def run_ours(args):
 
     # ---- plain one query per launch (latency form) on a subset
     single = {}
-    for tgt in TARGETS:
-        if args.skip_single or ("plain_f32", tgt) not in points:
-            continue
-        L, M = points[("plain_f32", tgt)]
-        for C in (1, 2, 4, 8):  # one CTA, or a cluster of C CTAs per query
-            lat = []
-            for i in range(300):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ix32.search(q[i:i + 1], K, L, M, stream=stream, cluster=C)
-                e1.record(stream)
-                e1.synchronize()
-                lat.append(e0.elapsed_time(e1) * 1e3)
-            single[f"{tgt}/cluster{C}"] = {"L": L, "M": M, "p50_us": float(np.percentile(lat, 50)),
-                                           "p99_us": float(np.percentile(lat, 99)),
-                                           "qps": 1e6 / float(np.mean(lat))}
-            try:
-                # the same 300 launches once more, untimed, with per-query counters: algorithmic bytes of
-                # a launch over its mean time, against the HBM peak
-                st1 = torch.empty((1, 8), dtype=torch.int64, device="cuda")
-                byts = 0.0
-                for i in range(300):
-                    ix32.search(q[i:i + 1], K, L, M, stream=stream, cluster=C, stats=st1)
-                    byts += algorithmic_bytes(st1.cpu().numpy(), w.R, ix32.info()["d_pad"] * 4, w.d, K, 0)
-                gbs = byts / (float(np.sum(lat)) * 1e-6) / 1e9
-                single[f"{tgt}/cluster{C}"].update({"gbs": gbs, "frac": gbs / peaks()[0]})
-            except Exception as e:  # the latency figures above stand without the byte count
-                log("single-query byte count skipped:", e)
+    if not args.skip_single:
+        single = latency_leg(torch, ix32, q, w, gt, calib, points, stream)
 
     # ---- end to end through the host-buffer C call (H2D + search + D2H)
     L, M = points[head]
@@ -653,6 +626,100 @@ def cheapest_points(torch, search, q, gt, Ls, Ms, targets, k=K):
 
 
 # ------------------------------------------------------ default-run legs
+
+def latency_leg(torch, ix, q, w, gt, calib, points, stream, n_lat=300):
+    """One query per launch, plain FP32 storage. For each recall target: the
+    throughput operating point on 1, 2, 4 and 8 CTAs per query, and the
+    latency operating point: the smallest L reaching the target on the
+    calibration queries at M = 64 (fewer, wider steps), on 4 and 8 CTAs.
+    Each is timed three ways over the same n_lat queries: CUDA events around
+    the Python call (host overhead included), CUDA events around the replay
+    of a CUDA graph holding the one launch, and the kernel's own device time
+    (globaltimer, query start to results written)."""
+    out = {}
+    ids = torch.empty((1, K), dtype=torch.int64, device="cuda")
+    dd = torch.empty((1, K), dtype=torch.float32, device="cuda")
+    st1 = torch.empty((1, 8), dtype=torch.int64, device="cuda")
+    qc = q[:calib]
+
+    def measure(L, M, C):
+        rec = {"L": L, "M": M, "cluster": C}
+        for i in range(20):
+            ix.search(q[i:i + 1], K, L, M, out=(ids, dd), stream=stream, cluster=C)
+        lat, dev, byts = [], [], 0.0
+        for i in range(n_lat):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.search(q[i:i + 1], K, L, M, out=(ids, dd), stream=stream, cluster=C)
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1) * 1e3)
+        for i in range(n_lat):
+            ix.search(q[i:i + 1], K, L, M, out=(ids, dd), stream=stream, cluster=C, stats=st1)
+            sn = st1.cpu().numpy()
+            dev.append((sn[0, 7] - sn[0, 6]) / 1e3)
+            byts += algorithmic_bytes(sn, w.R, ix.info()["d_pad"] * 4, w.d, K, 0)
+        rec.update({"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                    "qps": 1e6 / float(np.mean(lat)),
+                    "device_p50_us": float(np.percentile(dev, 50)), "device_p99_us": float(np.percentile(dev, 99))})
+        gbs = byts / (float(np.sum(lat)) * 1e-6) / 1e9
+        rec.update({"gbs": gbs, "frac": gbs / peaks()[0]})
+        try:
+            graphs = []
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            for i in range(n_lat):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=side):
+                    ix.search(q[i:i + 1], K, L, M, out=(ids, dd), cluster=C)
+                graphs.append(g)
+            torch.cuda.synchronize()
+            glat = []
+            for g in graphs:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                with torch.cuda.stream(stream):
+                    g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                glat.append(e0.elapsed_time(e1) * 1e3)
+            rec.update({"graph_p50_us": float(np.percentile(glat, 50)),
+                        "graph_p99_us": float(np.percentile(glat, 99))})
+            del graphs
+        except Exception as e:  # the figures above stand without the replay
+            log("single-query graph replay skipped:", e)
+        return rec
+
+    for tgt in TARGETS:
+        if ("plain_f32", tgt) not in points:
+            continue
+        L, M = points[("plain_f32", tgt)]
+        for C in (1, 2, 4, 8):
+            out[f"{tgt}/cluster{C}"] = measure(L, M, C)
+        # the latency operating point: M = 64, the smallest L that reaches the target on the calibration set
+        Ll = None
+        for Lc in L_SWEEP:
+            if Lc < K:
+                continue
+            r = recall_at_k(ix.search(qc, K, Lc, 64)[0].cpu().numpy(), gt[:calib])
+            if r >= tgt:
+                Ll = Lc
+                break
+        if Ll is not None:
+            for C in (4, 8):
+                out[f"{tgt}/latency_M64_cluster{C}"] = measure(Ll, 64, C)
+                out[f"{tgt}/latency_M64_cluster{C}"]["recall_calibration"] = r
+        best = min((v for k_, v in out.items() if k_.startswith(f"{tgt}/") and "graph_p50_us" in v),
+                   key=lambda v: v["graph_p50_us"], default=None)
+        if best is not None:
+            out[f"{tgt}/best"] = {"L": best["L"], "M": best["M"], "cluster": best["cluster"],
+                                  "graph_p50_us": best["graph_p50_us"], "p50_us": best["p50_us"],
+                                  "device_p50_us": best["device_p50_us"]}
+    return out
+
+
 
 def hot_vertices(adj, frac):
     """The round(frac * n) vertices with the most in-edges, ties to the smaller

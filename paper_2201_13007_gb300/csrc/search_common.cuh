@@ -567,6 +567,48 @@ __device__ void block_rank_sort(entry_t *in, int n, entry_t *out) {
     __syncthreads();
 }
 
+// Sorts in[0, n) ascending for n above a block's worth of entries: warps
+// sort runs of 32 in registers, then log2(n / 32) rounds merge adjacent runs
+// pairwise, each output placed by a merge-path co-rank search (ties taken
+// from the left run), ping-ponging between in and tmp (n entries each).
+// Returns the array holding the result; ends with a __syncthreads().
+template <int NT>
+__device__ entry_t *block_merge_sort(entry_t *in, int n, entry_t *tmp) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = (n + 31) >> 5;
+    for (int r = warp; r < S; r += NW) {
+        const int i = r * 32 + lane;
+        const entry_t v = warp_sort32(i < n ? in[i] : kEmptyEntry);
+        if (i < n) in[i] = v;
+    }
+    __syncthreads();
+    entry_t *src = in, *dst = tmp;
+    for (int w = 32; w < n; w <<= 1) {
+        for (int i = threadIdx.x; i < n; i += NT) {
+            const int p0 = i / (2 * w) * (2 * w);
+            const int o = i - p0;
+            const entry_t *A = src + p0;
+            const int a = min(w, n - p0);
+            const entry_t *B = A + a;
+            const int b = max(0, min(w, n - p0 - w));
+            int lo = max(0, o - b), hi = min(o, a);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] <= B[o - 1 - mid]) lo = mid + 1;
+                else hi = mid;
+            }
+            const int kk = o - lo;
+            dst[i] = (lo < a && (kk >= b || A[lo] <= B[kk])) ? A[lo] : B[kk];
+        }
+        __syncthreads();
+        entry_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
 // The k smallest of in[0..n) (k <= 32), ascending, at the front of the
 // returned array (fewer if n < k). Warp w sorts runs of 32 in registers and
 // keeps the first k of each in tmp; the c = ceil(n / 32) * k kept entries
@@ -980,8 +1022,9 @@ __device__ __forceinline__ int expand_step(const SearchArgs &a, uint32_t *table,
 }
 
 // The ns (> 0) survivors in surv, sorted by (key, id) (one warp for 32 or
-// fewer, warp runs plus binary-search ranks into `scratch` up to NT, else a
-// bitonic sort in place), are merged into the sorted queue Q[0..qlen): when
+// fewer, a bitonic sort in place up to 64, warp runs plus binary-search ranks
+// into `scratch` up to NT, else warp runs merged pairwise between surv and
+// `scratch`), are merged into the sorted queue Q[0..qlen): when
 // `unsafe` (the visited set may have forgotten a vertex) survivors whose id
 // is already queued, or repeated, are dropped first (counted in *dropped).
 // The first min(L, qlen + kept) entries go to Qn by merge path. *first_un
@@ -1005,6 +1048,8 @@ __device__ __forceinline__ int sort_dedupe_merge(const entry_t *Q, int qlen, ent
         // two barriers instead of a bitonic sort's dozen (at 64 or fewer the bitonic one is as cheap)
         block_rank_sort<NT>(surv, ns, scratch);
         srt = scratch;
+    } else if (ns > NT) {
+        srt = block_merge_sort<NT>(surv, ns, scratch);
     } else {
         int P = 64;
         while (P < ns) P <<= 1;
