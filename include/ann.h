@@ -123,8 +123,13 @@ typedef struct {
     const int32_t *order;
     /* Sync mode only: spread each query over a thread-block cluster of this
      * many CTAs (2, 4 or 8) that share the step's work through distributed
-     * shared memory (lower latency per query); 0 or 1 = one CTA per query.
-     * A clustered search is never persistent (one cluster per query). */
+     * shared memory (lower latency per query); 1 = one CTA per query;
+     * 0 = automatic: calls of 1 to 8 queries run on clusters of 8 CTAs (4 or
+     * 2 when the SMs are fewer than 8 per query) if the search is not
+     * persistent, asks for no phase counters, uses visited_mode 0 or 4 and
+     * the index has no neighbour groups; otherwise one CTA per query. The
+     * results do not depend on the choice. A clustered search is never
+     * persistent (one cluster per query). */
     int32_t cluster;
     /* Sync kernels only: device int64 array of nq x 4, or NULL. When given,
      * each query's SM clock cycles spent in its step phases are written
@@ -431,6 +436,27 @@ int ann_serve_submit(ann_server *server, const float *query, int32_t k, int32_t 
  * (>= 1), or ANN_ERR_TIMEOUT when nothing completed in time. Thread safe. */
 int ann_serve_poll(ann_server *server, ann_result *results, int64_t *out_ids, float *out_dists,
                    int32_t max, int32_t timeout_us);
+
+/* Drive a server with a request trace from native threads (a load
+ * generator without the caller's per-request overhead): request i asks for
+ * row qi[i] of the host array queries (n_queries x d float32) with k[i],
+ * L[i], M[i], and is submitted arrival_us[i] microseconds after the call
+ * starts (host steady clock; arrival_us non-decreasing, or NULL to submit
+ * every request as fast as the server accepts it). A submission that finds
+ * every slot taken is retried until one frees. The calling thread collects
+ * the completions meanwhile. Outputs, per request (host arrays of nreq):
+ * latency_us (submit to completion, as ann_result.latency_us), device_us,
+ * and status; *wall_us is the time from the start to the last completion;
+ * *busy_retries (may be NULL) counts the retried submissions. The server
+ * must have no other client during the call. Synchronous. Errors:
+ * ANN_ERR_ARG; ANN_ERR_TIMEOUT if the trace is not complete 60 s after its
+ * last arrival (requests still in flight are then collected by later
+ * ann_serve_poll calls). The paper has no counterpart (it measures one
+ * query at a time). */
+int ann_serve_replay(ann_server *server, const float *queries, int64_t n_queries, const int64_t *qi,
+                     const int32_t *k, const int32_t *L, const int32_t *M, const double *arrival_us,
+                     int64_t nreq, double *latency_us, double *device_us, int32_t *status, double *wall_us,
+                     int64_t *busy_retries);
 
 #ifdef __cplusplus
 }

@@ -212,6 +212,22 @@ int plan_search(const ann_index *index, const float *queries, int64_t nq, int32_
     if (p->merge_rule == 1 && !(p->patience >= 0.f))
         return fail(ANN_ERR_ARG, "patience must be >= 0 (or INFINITY) with merge_rule 1");
     if (async && M > 32) return fail(ANN_ERR_ARG, "async mode runs one warp per walker: M=%d > 32", M);
+    // cluster = 0 and at most 8 queries: each query on a cluster of 8 CTAs (4, 2 if fewer SMs), which the
+    // one-query latency measurements favour at every (L, M), when the cluster kernel runs the search as asked
+    // (sync, not persistent, no phase counters, no neighbour groups, a set-associative visited set); the
+    // results are those of one CTA per query. If that plan does not fit, one CTA per query.
+    if (p->cluster == 0 && nq >= 1 && nq <= 8 && !async && !p->persistent && !p->phase_cycles &&
+        (p->visited_mode == 0 || p->visited_mode == 4) && x.n_hot == 0) {
+        for (int c = 8; c >= 2; c >>= 1) {
+            if ((int64_t)nq * c > sm_count()) continue;
+            ann_search_params pc = *p;
+            pc.cluster = c;
+            const std::string saved = g_err;
+            if (plan_search(index, queries, nq, k, L, M, out_ids, out_dists, &pc, plan) == ANN_OK) return ANN_OK;
+            g_err = saved;
+            break;
+        }
+    }
     const int csize = p->cluster > 1 ? p->cluster : 1;
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8)
         return fail(ANN_ERR_ARG, "cluster=%d not in {0, 1, 2, 4, 8}", p->cluster);

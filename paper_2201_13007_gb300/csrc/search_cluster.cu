@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_search_kernel(const SearchArgs 
     for (;;) {
         const int par = step & 1;
         // --- select (every CTA, identical): the first Mcur unchecked entries, all warps scanning
-        const int found = select_unchecked<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
+        const int found = select_step<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
                                                &ctl.sel_last);
         ANN_CPHASE(0)
         const int nact = found < Mcur ? found : Mcur;

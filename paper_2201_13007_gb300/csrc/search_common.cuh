@@ -917,14 +917,13 @@ __device__ __forceinline__ int select_unchecked(const entry_t *Q, int qlen, int 
         const unsigned bal = __ballot_sync(kFull, un);
         if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
-        int c = lane < NW ? wcnt[lane] : 0;
+        int total = 0, pre = 0;
 #pragma unroll
-        for (int o = 1; o < NW; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, c, o);
-            if (lane >= o) c += v;
+        for (int w2 = 0; w2 < NW; ++w2) {
+            const int c = wcnt[w2];
+            total += c;
+            pre += w2 < warp ? c : 0;
         }
-        const int total = __shfl_sync(kFull, c, NW - 1);
-        const int pre = warp > 0 ? __shfl_sync(kFull, c, warp - 1) : 0;
         const int r = found + pre + __popc(bal & lt_mask);
         const bool take = un && r < Mcur;
         if (take) {
@@ -937,6 +936,44 @@ __device__ __forceinline__ int select_unchecked(const entry_t *Q, int qlen, int 
         __syncthreads();
     }
     return found;
+}
+
+// The same selection scanned by warp 0 alone, 32 entries per round, then
+// one barrier. With eight warps or fewer (the small CTAs that run many
+// queries per SM) this keeps the step's live state in registers; the
+// block-wide scan above serves the larger CTAs that run one query alone.
+template <int NW>
+__device__ __forceinline__ int select_step(const entry_t *Q, int qlen, int first_un, int Mcur, int *sel_id,
+                                           int *sel_pos, int *wcnt, int *sel_last) {
+    if constexpr (NW >= 16) {
+        return select_unchecked<NW>(Q, qlen, first_un, Mcur, sel_id, sel_pos, wcnt, sel_last);
+    } else {
+        const int lane = threadIdx.x & 31;
+        if ((threadIdx.x >> 5) == 0) {
+            int found = 0, last_pos = -1;
+            for (int b = first_un & ~31; b < qlen && found < Mcur; b += 32) {
+                const int i = b + lane;
+                const entry_t e = i < qlen ? Q[i] : kChecked;
+                const bool un = !(e & kChecked);
+                const unsigned bal = __ballot_sync(kFull, un);
+                const int r = found + __popc(bal & ((1u << lane) - 1u));
+                const bool take = un && r < Mcur;
+                if (take) {
+                    sel_id[r] = (int)entry_id(e);
+                    sel_pos[r] = i;
+                }
+                const unsigned tb = __ballot_sync(kFull, take);
+                if (tb) last_pos = b + 31 - __clz(tb);
+                found += __popc(bal);
+            }
+            if (lane == 0) {
+                wcnt[0] = found;
+                *sel_last = last_pos;
+            }
+        }
+        __syncthreads();
+        return wcnt[0];
+    }
 }
 
 template <int NW>

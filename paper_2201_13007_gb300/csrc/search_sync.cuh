@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) sync_search_kernel(cons
             const int par = step & 1;
             // --- select: the first Mcur unchecked entries (rank order) of the stable queue, all warps
             // scanning from first_un (entries before it are all checked)
-            const int found = select_unchecked<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
+            const int found = select_step<NW>(Q, qlen, ctl.first_un, Mcur, sel_id, sel_pos, ctl.wcnt,
                                                    &ctl.sel_last);
             const int nact = found < Mcur ? found : Mcur;
             if (nact == 0) break;  // no unchecked vertex left (identical in every warp)
