@@ -183,19 +183,19 @@ def max_over_ranks(torch, dist, seconds, device="cuda"):
 
 
 def kernel_sources_digest():
-    """Short SHA-256 of the CUDA sources and the C header: an ncu figure is
-    only reused while the code it was taken from is unchanged."""
+    """Short SHA-256 of the headline kernel's own sources (its translation
+    unit and the headers it includes from the package): an ncu figure is only
+    reused while the code it was taken from is unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2201_13007_gb300", "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
-    for f in files + [os.path.join(ROOT, "include", "ann.h")]:
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for f in ("search_sync_bf16.cu", "search_sync.cuh", "search_common.cuh", "ann_internal.cuh"):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-TRAFFIC_SIDECAR = os.path.join(ROOT, "profiles", "sync_search_kernel_sift1m_L640_M32_bf16.traffic.json")
+TRAFFIC_SIDECAR = os.path.join(ROOT, "profiles", "sync_search_kernel_sift1m_L576_M32_bf16.traffic.json")
 
 
 def profiled_traffic(kernel_label):
@@ -451,7 +451,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": h["gbs_exact_visited"], "peak": hbm, "unit": "GB/s",
                      "frac": h["gbs_exact_visited"] / hbm, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "traffic": profiled_traffic(klabel),
-                     "traffic_source": "profiles/sync_search_kernel_sift1m_L640_M32_bf16.traffic.json (one ncu "
+                     "traffic_source": "profiles/sync_search_kernel_sift1m_L576_M32_bf16.traffic.json (one ncu "
                                        "capture, dram__bytes_read.sum + dram__bytes_write.sum per launch)",
                      "kernel": klabel,
                      "bytes": "the method's own work: sum over queries of E_exp*R*4 + E_dist*row_bytes + L*d*4 "
@@ -1062,7 +1062,6 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
     and checked on 2,000 held-out ones; latency percentiles at five offered
     rates (0.1 .. 0.9 of the measured saturation rate)."""
     import ctypes
-    import threading as th
     from paper_2201_13007_gb300 import _abi, synth
     from paper_2201_13007_gb300.index import Index
     t0 = time.time()
@@ -1102,40 +1101,19 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
     cfg = _abi.ServeConfig(max_batch=512, streams=4, max_k=100, max_L=int(LL.max()), max_M=16)
 
     def run(rate):
+        """One pass of the trace through a fresh server, driven from native threads (ann_serve_replay):
+        Poisson arrivals at `rate` requests/s, or every request as fast as the server takes it (rate 0)."""
         srv = ctypes.c_void_p(_abi.ann_serve_create(ix.handle, cfg))
-        done = []
-        stop = th.Event()
-
-        def poller():
-            res = (_abi.Result * 256)()
-            ids = np.zeros((256, 100), np.int64)
-            d = np.zeros((256, 100), np.float32)
-            while not (stop.is_set() and len(done) >= nreq):
-                got = _abi.ann_serve_poll(srv, res, ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(d.ctypes.data),
-                                          256, 2000)
-                for i in range(got):
-                    done.append((res[i].latency_us, res[i].device_us))
-        pt = th.Thread(target=poller)
-        pt.start()
-        arr = np.cumsum(g.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq)
-        t0 = time.perf_counter()
-        busy = 0
-        for i in range(nreq):
-            while rate and time.perf_counter() - t0 < arr[i]:
-                pass
-            qv = queries[qi[i]]
-            while _abi.ann_serve_submit(srv, ctypes.c_void_p(qv.ctypes.data), int(ks[i]), int(LL[i]), int(MM[i]), i) \
-                    == _abi.ANN_ERR_BUSY:
-                busy += 1
-        stop.set()
-        pt.join()
-        wall = time.perf_counter() - t0
-        _abi.ann_serve_destroy(srv)
-        lat = np.array([x[0] for x in done])
-        dev = np.array([x[1] for x in done])
-        return {"offered_qps": rate, "achieved_qps": nreq / wall, "p50_us": float(np.percentile(lat, 50)),
+        arr = np.cumsum(g.exponential(1e6 / rate, nreq)) if rate else None
+        try:
+            lat, dev, stt, wall_us, busy = _abi.ann_serve_replay(srv, queries, qi, ks, LL, MM, arr)
+        finally:
+            _abi.ann_serve_destroy(srv)
+        if not (stt == 0).all():
+            raise RuntimeError(f"{int((stt != 0).sum())} requests failed")
+        return {"offered_qps": rate, "achieved_qps": nreq / (wall_us * 1e-6), "p50_us": float(np.percentile(lat, 50)),
                 "p99_us": float(np.percentile(lat, 99)), "device_p50_us": float(np.percentile(dev, 50)),
-                "device_p99_us": float(np.percentile(dev, 99)), "busy_retries": busy}
+                "device_p99_us": float(np.percentile(dev, 99)), "busy_retries": int(busy)}
 
     sat = run(0)  # flood: every request submitted as fast as the client can
     sat["hbm_gbs"] = sat["achieved_qps"] * bytes_per_req / 1e9
@@ -1158,7 +1136,8 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
             "repair_links": added,
             "hbm": "saturation QPS x mean algorithmic bytes per request (adjacency rows of expanded vertices + "
                    "one BF16 row per distance, counted on the held-out sample) / measured copy bandwidth",
-            "client": "one Python thread submitting through ctypes, one polling"}
+            "client": "ann_serve_replay: one native thread submitting at the trace's arrival times, the calling "
+                      "thread polling"}
 
 
 def run_serve(args):
