@@ -118,6 +118,7 @@ def lib():
             L.ann_serve_destroy.restype = None
             L.ann_serve_submit.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint64]
             L.ann_serve_poll.argtypes = [vp, ctypes.POINTER(Result), vp, vp, i32, i32]
+            L.ann_serve_replay.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
             L.ann_last_error.restype = ctypes.c_char_p
             L.ann_last_error.argtypes = []
             _lib = L
@@ -203,6 +204,31 @@ def ann_serve_poll(server, results, out_ids, out_dists, max_n, timeout_us) -> in
     if rc < 0:
         _check(rc)
     return rc
+
+
+def ann_serve_replay(server, queries, qi, k, L, M, arrival_us=None):
+    """Drive the server with a request trace from native threads
+    (ann_serve_replay). queries: host float32 (n, d); qi, k, L, M: one entry
+    per request; arrival_us: submit times after the start (None = flood).
+    Returns (latency_us, device_us, status, wall_us, busy_retries)."""
+    import numpy as np
+    q = np.ascontiguousarray(queries, np.float32)
+    qi = np.ascontiguousarray(qi, np.int64)
+    k = np.ascontiguousarray(k, np.int32)
+    L = np.ascontiguousarray(L, np.int32)
+    M = np.ascontiguousarray(M, np.int32)
+    n = qi.shape[0]
+    arr = None if arrival_us is None else np.ascontiguousarray(arrival_us, np.float64)
+    lat = np.empty(n, np.float64)
+    dev = np.empty(n, np.float64)
+    st = np.empty(n, np.int32)
+    wall = ctypes.c_double(0.0)
+    busy = ctypes.c_int64(0)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(lib().ann_serve_replay(server, p(q), q.shape[0], p(qi), p(k), p(L), p(M),
+                                  None if arr is None else p(arr), n, p(lat), p(dev), p(st),
+                                  ctypes.byref(wall), ctypes.byref(busy)))
+    return lat, dev, st, wall.value, busy.value
 
 
 def ann_batch_create(index, nq, k, L, M, buckets, n_buckets, params) -> int:

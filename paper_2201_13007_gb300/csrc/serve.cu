@@ -13,6 +13,7 @@
 // others are running are admitted as soon as a group frees up and overlap
 // with the work already on the GPU. No kernel or copy waits on another
 // group; the host thread only polls events.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
@@ -381,6 +382,75 @@ int ann_serve_poll(ann_server *s, ann_result *results, int64_t *out_ids, float *
         n++;
     }
     return n;
+}
+
+
+int ann_serve_replay(ann_server *s, const float *queries, int64_t n_queries, const int64_t *qi, const int32_t *k,
+                     const int32_t *L, const int32_t *M, const double *arrival_us, int64_t nreq, double *latency_us,
+                     double *device_us, int32_t *status, double *wall_us, int64_t *busy_retries) {
+    if (!s || !queries || !qi || !k || !L || !M || !latency_us || !device_us || !status || !wall_us || nreq < 0 ||
+        n_queries < 1)
+        return serve_fail(ANN_ERR_ARG, "server, queries, trace and output arrays must be valid");
+    for (int64_t i = 0; i < nreq; ++i) {
+        if (qi[i] < 0 || qi[i] >= n_queries) return serve_fail(ANN_ERR_ARG, "qi[%lld] outside the queries", (long long)i);
+        if (arrival_us && (!(arrival_us[i] >= 0.0) || (i > 0 && arrival_us[i] < arrival_us[i - 1])))
+            return serve_fail(ANN_ERR_ARG, "arrival_us must be non-negative and non-decreasing");
+        latency_us[i] = device_us[i] = std::numeric_limits<double>::quiet_NaN();
+        status[i] = ANN_ERR_STATE;  // not completed
+    }
+    const double t0 = now_us();
+    const double deadline = t0 + (nreq && arrival_us ? arrival_us[nreq - 1] : 0.0) + 60e6;
+    const int d = s->info.d;
+    std::atomic<int64_t> retries{0};
+    std::atomic<bool> give_up{false};
+    std::atomic<int> submit_rc{ANN_OK};
+    std::thread submitter([&] {
+        for (int64_t i = 0; i < nreq && !give_up.load(); ++i) {
+            if (arrival_us)
+                while (now_us() - t0 < arrival_us[i]) {
+                }
+            for (;;) {
+                const int rc = ann_serve_submit(s, queries + (size_t)qi[i] * d, k[i], L[i], M[i], (uint64_t)i);
+                if (rc == ANN_OK) break;
+                if (rc != ANN_ERR_BUSY || now_us() > deadline || give_up.load()) {
+                    submit_rc.store(rc == ANN_ERR_BUSY ? ANN_ERR_TIMEOUT : rc);
+                    give_up.store(true);
+                    return;
+                }
+                retries.fetch_add(1);
+            }
+        }
+    });
+    const int B = 256;
+    std::vector<ann_result> res(B);
+    std::vector<int64_t> ids((size_t)B * s->cfg.max_k);
+    std::vector<float> dd((size_t)B * s->cfg.max_k);
+    int64_t got = 0;
+    double t_last = t0;
+    while (got < nreq && !give_up.load() && now_us() < deadline) {
+        const int n = ann_serve_poll(s, res.data(), ids.data(), dd.data(), B, 1000);
+        for (int j = 0; j < n; ++j) {
+            const uint64_t t = res[j].tag;
+            if (t >= (uint64_t)nreq) continue;
+            latency_us[t] = res[j].latency_us;
+            device_us[t] = res[j].device_us;
+            status[t] = res[j].status;
+            ++got;
+        }
+        if (n > 0) t_last = now_us();
+    }
+    give_up.store(true);
+    submitter.join();
+    *wall_us = t_last - t0;
+    if (busy_retries) *busy_retries = retries.load();
+    if (submit_rc.load() != ANN_OK && got < nreq) {
+        const int rc = submit_rc.load();
+        return rc == ANN_ERR_TIMEOUT ? serve_fail(ANN_ERR_TIMEOUT, "replay: the server took no request for 60 s")
+                                     : rc;
+    }
+    if (got < nreq) return serve_fail(ANN_ERR_TIMEOUT, "replay: %lld of %lld requests completed in time",
+                                      (long long)got, (long long)nreq);
+    return ANN_OK;
 }
 
 }  // extern "C"

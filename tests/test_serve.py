@@ -143,3 +143,31 @@ def test_scratch_budget_limits_groups(setup):
         _abi.ann_serve_destroy(srv)
     with pytest.raises(_abi.AnnError):
         _server(ix, max_batch=8, streams=2, max_k=10, max_L=32, max_M=2, scratch_bytes=per_group // 2)
+
+
+def test_trace_replay_completes_every_request(setup):
+    """ann_serve_replay drives the server from native threads: every request
+    of a flood trace and of a Poisson trace completes with ANN_OK, each
+    latency is at least its device time, and the timed window covers the
+    last arrival. The results themselves are the server's (compared with
+    standalone searches above)."""
+    ix, w = setup
+    srv = _server(ix, max_batch=64, streams=2, max_k=10, max_L=128, max_M=8, slots=256)
+    try:
+        g = np.random.default_rng(3)
+        n = 600
+        qi = g.integers(0, w.queries.shape[0], n)
+        k = np.full(n, 10, np.int32)
+        L = g.choice([32, 64, 128], n).astype(np.int32)
+        M = g.choice([1, 4, 8], n).astype(np.int32)
+        lat, dev, st, wall, busy = _abi.ann_serve_replay(srv, w.queries, qi, k, L, M)
+        assert (st == 0).all() and np.isfinite(lat).all() and (lat >= dev).all() and wall > 0
+        arr = np.cumsum(g.exponential(1e6 / 20000.0, n))
+        lat, dev, st, wall, busy = _abi.ann_serve_replay(srv, w.queries, qi, k, L, M, arr)
+        assert (st == 0).all() and np.isfinite(lat).all() and wall >= arr[-1]
+        with pytest.raises(_abi.AnnError):
+            _abi.ann_serve_replay(srv, w.queries, qi, k, L, M, arr[::-1].copy())  # arrivals must not decrease
+        with pytest.raises(_abi.AnnError):
+            _abi.ann_serve_replay(srv, w.queries, qi + w.queries.shape[0], k, L, M)  # rows out of range
+    finally:
+        _abi.ann_serve_destroy(srv)
