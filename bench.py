@@ -1106,6 +1106,7 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
         srv = ctypes.c_void_p(_abi.ann_serve_create(ix.handle, cfg))
         arr = np.cumsum(g.exponential(1e6 / rate, nreq)) if rate else None
         try:
+            _abi.ann_serve_replay(srv, queries, qi[:500], ks[:500], LL[:500], MM[:500])  # warm-up, untimed
             lat, dev, stt, wall_us, busy = _abi.ann_serve_replay(srv, queries, qi, ks, LL, MM, arr)
         finally:
             _abi.ann_serve_destroy(srv)

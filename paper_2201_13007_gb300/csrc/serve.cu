@@ -144,6 +144,7 @@ void launch_group(ann_server *s, Group &g) {
         p.mode = s->cfg.mode;
         p.rerank = s->cfg.rerank;
         p.R_ratio = 0.8f;
+        p.cluster = 1;  // one CTA per request: groups run side by side and share the SMs
         p.k_per_query = g.d_kLM;
         p.L_per_query = g.d_kLM + B;
         p.M_per_query = g.d_kLM + 2 * B;
@@ -228,8 +229,10 @@ void scheduler(ann_server *s) {
         }
         if (s->stop && s->pending.empty() && !any_busy) break;
         if (any_busy) {
+            // poll the groups' events again at once: a timed sleep rounds up to the kernel's timer slack
+            // (tens of microseconds), which every request would wait on top of its search
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            std::this_thread::yield();
         } else {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->stop || !s->pending.empty(); });
         }
