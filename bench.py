@@ -828,6 +828,13 @@ def deep_batch_leg(torch, args):
     with torch.cuda.graph(graph):
         b.search(q, out=(ids, dists))
     t_graph = float(np.mean(event_time(torch, graph.replay, max(3, args.steps // 4), 2, flush)))
+    # the method's bytes for the same plan, from per-query counters of an untimed run
+    st = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
+    Batch(ix, k, L, M, buckets=cfg, stats=st).search(q)
+    torch.cuda.synchronize()
+    sn = st.cpu().numpy()
+    byts = float((sn[:, 1] * w.R * 4 + sn[:, 2] * ix.info()["d_pad"] * 4).sum() + nq * w.d * 4 + (k * 12).sum())
+    hbm, _ = peaks()
     sample = np.arange(0, nq, 100)
     gt = exact_topk_gpu(w.base, w.queries[sample], 100, torch, metric="ip")
     idn = ids.cpu().numpy()
@@ -846,6 +853,9 @@ def deep_batch_leg(torch, args):
     return {"workload": "deep-like 1M x 96 unit vectors (inner product), 100,000 queries, k in {1,10,100}, "
                         "L in {32..1024}, M in {1..32}", "buckets": cfg, "tune_s": tune_s,
             "graph_replay_qps": nq / t_graph, "ms_per_step": t_graph * 1e3,
+            "gbs": byts / t_graph / 1e9, "frac": byts / t_graph / 1e9 / hbm,
+            "bytes": "sum over queries of E_exp*R*4 + E_dist*row_bytes (FP32 rows) + d*4 + k*12, counters of an "
+                     "untimed run of the same plan",
             "mean_recall@k_sample": float(rec), "recall_sample": int(sample.size),
             "one_launch_per_query": {"qps": 1e6 / float(np.mean(lat)), "p50_us": float(np.percentile(lat, 50)),
                                      "p99_us": float(np.percentile(lat, 99)), "sample": len(lat)}}
