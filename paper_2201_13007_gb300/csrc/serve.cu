@@ -6,13 +6,15 @@
 // pinned host mirrors and a completion event. A scheduler thread
 //   - harvests groups whose event has fired (results copied out, latency
 //     taken, completions queued for ann_serve_poll),
-//   - fills every free group with waiting requests and launches it:
+//   - fills every free group with waiting requests (the oldest and those of
+//     its cost class: L in the same power-of-two range) and launches it:
 //     H2D copy of the batch, one search launch with per-query k / L / M, D2H
 //     copy of results and counters, event record -- all on the group's stream.
 // Groups run concurrently on the device, so requests that arrive while
 // others are running are admitted as soon as a group frees up and overlap
 // with the work already on the GPU. No kernel or copy waits on another
 // group; the host thread only polls events.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -76,7 +78,10 @@ struct ann_server {
     std::vector<Group> groups;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending;
+    // waiting requests, one queue per cost class (L in the same power-of-two range: L <= 2048)
+    static constexpr int kClasses = 12;
+    std::deque<Request> pending[kClasses];
+    int64_t npending = 0;
     std::deque<Done> done;
     int64_t accepted = 0;  // submitted and not yet collected
     bool stop = false;
@@ -126,6 +131,13 @@ size_t group_device_bytes(int B, int d, int kmax) {
 }
 
 // Copy the batch in, search, copy results out, record the event.
+// Requests whose queue lengths share a power-of-two range share launches.
+int cost_class(int L) {
+    int c = 0;
+    while ((1 << c) < L) ++c;
+    return c;
+}
+
 void launch_group(ann_server *s, Group &g) {
     const int B = (int)g.reqs.size(), d = s->info.d, kmax = s->cfg.max_k;
     for (int i = 0; i < B; ++i) {
@@ -214,27 +226,34 @@ void scheduler(ann_server *s) {
             fresh.clear();
             s->cv_done.notify_all();
         }
-        // admit waiting requests into every free group
+        // admit waiting requests into every free group: the oldest request and the waiting ones of its cost
+        // class (queue length L in the same power-of-two range), oldest first, so that short searches do not
+        // wait for a long one in the same launch
         for (Group &g : s->groups) {
-            if (g.busy || s->pending.empty()) continue;
-            const int take = (int)std::min<size_t>(s->pending.size(), (size_t)s->cfg.max_batch);
-            for (int i = 0; i < take; ++i) {
-                g.reqs.push_back(std::move(s->pending.front()));
-                s->pending.pop_front();
+            if (g.busy || s->npending == 0) continue;
+            int cls = -1;
+            for (int c = 0; c < ann_server::kClasses; ++c)
+                if (!s->pending[c].empty() && (cls < 0 || s->pending[c].front().t_submit < s->pending[cls].front().t_submit))
+                    cls = c;
+            std::deque<Request> &pq = s->pending[cls];
+            while (!pq.empty() && (int)g.reqs.size() < s->cfg.max_batch) {
+                g.reqs.push_back(std::move(pq.front()));
+                pq.pop_front();
+                s->npending--;
             }
             lk.unlock();
             launch_group(s, g);
             any_busy = true;
             lk.lock();
         }
-        if (s->stop && s->pending.empty() && !any_busy) break;
+        if (s->stop && s->npending == 0 && !any_busy) break;
         if (any_busy) {
             // poll the groups' events again at once: a timed sleep rounds up to the kernel's timer slack
             // (tens of microseconds), which every request would wait on top of its search
             lk.unlock();
             std::this_thread::yield();
         } else {
-            s->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->stop || !s->pending.empty(); });
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->stop || s->npending > 0; });
         }
     }
 }
@@ -356,7 +375,8 @@ int ann_serve_submit(ann_server *s, const float *query, int32_t k, int32_t L, in
         if (s->stop) return serve_fail(ANN_ERR_STATE, "server is shutting down");
         if (s->accepted >= s->cfg.slots) return serve_fail(ANN_ERR_BUSY, "all %d request slots are taken", s->cfg.slots);
         r.t_submit = now_us();
-        s->pending.push_back(std::move(r));
+        s->pending[cost_class(r.L)].push_back(std::move(r));
+        s->npending++;
         s->accepted++;
     }
     s->cv_work.notify_one();
