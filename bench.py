@@ -732,7 +732,6 @@ def hot_vertices(adj, frac):
 
 
 def grouping_leg(torch, w, ix, kw, point, q, flush, args):
-    import oracle
     L, M = point
     nq = q.shape[0]
     ids0, d0 = ix.search(q, K, L, M, **kw)
@@ -746,18 +745,9 @@ def grouping_leg(torch, w, ix, kw, point, q, flush, args):
         out[f"hot{frac}_{pf}"] = {"ms": t * 1e3, "qps": nq / t, "speedup": t_plain / t,
                                   "same_answers": bool(torch.equal(ids, ids0) and torch.equal(d, d0))}
     ix.group_neighbors(0.0)
-    # how many expansions land on a grouped vertex (the oracle's expansion order on a sample of queries)
-    hot = np.zeros(w.n, bool)
-    hot[hot_vertices(w.adj, frac)] = True
-    oracle.build()
-    ex = hit = 0
-    for i in range(0, nq, nq // 24):
-        tr = oracle.search_trace(w.base, w.adj, w.entry, w.queries[i], algo="topm", L=L, K=K, M0=1, M_max=M, t=1)
-        ex += tr["expanded"].size
-        hit += int(hot[tr["expanded"]].sum())
-    out["hot_fraction_of_expansions"] = hit / max(ex, 1)
-    out["hot_vertices"] = int(hot.sum())
-    out["extra_hbm_bytes"] = int(hot.sum()) * w.R * ix.info()["d_pad"] * 2
+    H = hot_vertices(w.adj, frac).size
+    out["hot_vertices"] = int(H)
+    out["extra_hbm_bytes"] = int(H) * w.R * ix.info()["d_pad"] * 2
     return out
 
 
