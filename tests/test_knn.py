@@ -36,19 +36,19 @@ def _gpu_knn(base_bits, q_bits, self_offset, metric, k):
     return ids.cpu().numpy().astype(np.int64), dist.cpu().numpy()
 
 
-def _oracle_knn(base, q, self_offset, metric, k):
+def _oracle_knn(base, q, self_offset, metric, k, extra=0):
     """Oracle answer with each query's own row removed when the queries are
-    rows of the base set."""
+    rows of the base set; `extra` more keys past the k-th (+inf if none)."""
     n = base.shape[0]
-    kk = min(k + 1, n) if self_offset >= 0 else min(k, n)
+    kk = min(k + extra + 1, n) if self_offset >= 0 else min(k + extra, n)
     ids, keys = oracle.exact_knn(base, q, kk, metric=metric, nthreads=8)
-    out_i = np.full((q.shape[0], k), -1, np.int64)
-    out_k = np.full((q.shape[0], k), np.inf)
+    out_i = np.full((q.shape[0], k + extra), -1, np.int64)
+    out_k = np.full((q.shape[0], k + extra), np.inf)
     for r in range(q.shape[0]):
         m = ids[r] >= 0
         if self_offset >= 0:
             m &= ids[r] != self_offset + r
-        ii, kv = ids[r][m][:k], keys[r][m][:k]
+        ii, kv = ids[r][m][:k + extra], keys[r][m][:k + extra]
         out_i[r, :ii.size] = ii
         out_k[r, :kv.size] = kv
     return out_i, out_k
@@ -111,7 +111,8 @@ def test_knn_unit_rows_within_fp32_bound(case):
     base, bits, q, qbits, self_offset, metric, k = _setup(case, _unit_rows)
     d = base.shape[1]
     gi, gd = _gpu_knn(bits, qbits, self_offset, metric, k)
-    oi, ok = _oracle_knn(base, q, self_offset, metric, k)
+    oi, ok_all = _oracle_knn(base, q, self_offset, metric, k, extra=1)
+    oi, ok, k_next = oi[:, :k], ok_all[:, :k], ok_all[:, k]
     # FP32 error of |q|^2 + |x|^2 - 2<q, x> (or -<q, x>) for unit-norm rows:
     # at most (d + 2) u (|q| + |x|)^2 = 4 (d + 2) u; swaps need twice that.
     tol = 2.0 * 4.0 * (d + 2) * 2.0 ** -24
@@ -130,7 +131,7 @@ def test_knn_unit_rows_within_fp32_bound(case):
         # a rank whose oracle key stands clear of both neighbours must hold the same id
         kr = ok[r]
         gap_lo = np.r_[np.inf, np.diff(kr)]
-        gap_hi = np.r_[np.diff(kr), np.inf]
+        gap_hi = np.r_[np.diff(kr), k_next[r] - kr[-1]]  # the last rank against the (k+1)-th key
         clear = (gap_lo > tol) & (gap_hi > tol)
         assert np.array_equal(ids[clear], oi[r][clear]), r
 
