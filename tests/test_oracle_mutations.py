@@ -46,3 +46,44 @@ def test_mutant_is_caught(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+# Planted mistakes in the FP64 block-by-block k-NN of oracle/__init__.py (the
+# 10M spot check's reference): each mutant of exact_knn_blocked, rebuilt from
+# its own source with one edit, must fail the blocked pins of
+# test_oracle_pins.py (integer data with tie runs cut by blocks; float data).
+PY_MUTATIONS = {
+    "block_cut_drops_ties": ("rows, cols = torch.nonzero(D <= kth[:, None], as_tuple=True)",
+                             "rows, cols = torch.nonzero(D < kth[:, None], as_tuple=True)"),
+    "query_norm_dropped": ("vals = vals + qn[c:c + qchunk][rows]", "vals = vals + 0.0"),
+    "block_offset_dropped": ("cand_i[c + r].append(cols[m].astype(np.int64) + a)",
+                             "cand_i[c + r].append(cols[m].astype(np.int64))"),
+    "order_by_id_first": ("o = np.lexsort((ci, ck))[:K]", "o = np.lexsort((ck, ci))[:K]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_blocked_knn_mutant_is_caught(name):
+    import inspect
+    import types
+
+    import numpy as np
+
+    import oracle
+    import test_oracle_pins as pins
+
+    old, new = PY_MUTATIONS[name]
+    src = inspect.getsource(oracle.exact_knn_blocked)
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    ns = dict(oracle.__dict__)
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    mut = types.SimpleNamespace(exact_knn=oracle.exact_knn, exact_knn_blocked=ns["exact_knn_blocked"], np=np)
+    caught = False
+    for check in (lambda: pins.test_exact_knn_blocked_equals_the_plain_sum_on_integer_data(mut, "l2"),
+                  lambda: pins.test_exact_knn_blocked_equals_the_plain_sum_on_integer_data(mut, "ip"),
+                  lambda: pins.test_exact_knn_blocked_float_data_and_padding(mut)):
+        try:
+            check()
+        except AssertionError:
+            caught = True
+    assert caught, f"mutant {name} passed every blocked pin"
