@@ -84,6 +84,44 @@ def test_blocked_knn_mutant_is_caught(name):
                   lambda: pins.test_exact_knn_blocked_float_data_and_padding(mut)):
         try:
             check()
-        except AssertionError:
+        except Exception:  # a failed assertion, or a mutant that cannot even fill its output
             caught = True
     assert caught, f"mutant {name} passed every blocked pin"
+
+
+GEMM_MUTATIONS = {
+    "tie_cut_strict": ("cand = np.flatnonzero(D[r] <= kth)", "cand = np.flatnonzero(D[r] < kth)"),
+    "query_norm_dropped": ('D = xn[None, :] - 2.0 * dot + np.einsum("ij,ij->i", q, q)[:, None]',
+                           "D = xn[None, :] - 2.0 * dot"),
+    "order_by_id_first": ("o = np.lexsort((cand, D[r, cand]))[:kk]", "o = np.lexsort((D[r, cand], cand))[:kk]"),
+    "dot_sign": ('D = xn[None, :] - 2.0 * dot + np.einsum', 'D = xn[None, :] + 2.0 * dot + np.einsum'),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GEMM_MUTATIONS))
+def test_gemm_knn_mutant_is_caught(name):
+    """The same for exact_knn_gemm (the 1M-point recall ground truth of the
+    full-size tests): each mutant fails one of its pins."""
+    import inspect
+    import types
+
+    import numpy as np
+
+    import oracle
+    import test_oracle_pins as pins
+
+    old, new = GEMM_MUTATIONS[name]
+    src = inspect.getsource(oracle.exact_knn_gemm)
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    ns = dict(oracle.__dict__)
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    mut = types.SimpleNamespace(exact_knn=oracle.exact_knn, exact_knn_gemm=ns["exact_knn_gemm"], np=np)
+    caught = False
+    for check in (lambda: pins.test_exact_knn_gemm_equals_the_plain_sum_on_integer_data(mut, "l2"),
+                  lambda: pins.test_exact_knn_gemm_equals_the_plain_sum_on_integer_data(mut, "ip"),
+                  lambda: pins.test_exact_knn_gemm_float_data_within_fp64_rounding(mut)):
+        try:
+            check()
+        except Exception:  # a failed assertion, or a mutant that cannot even fill its output
+            caught = True
+    assert caught, f"mutant {name} passed every GEMM pin"
