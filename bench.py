@@ -359,14 +359,15 @@ def run_ours(args):
     # at the cheapest points of a sweep on this workload (one walker per warp)
     async_pts = {}
     if ix16 is not None and not args.point:
-        for tgt, (L, M) in ((0.9, (128, 4)), (0.99, (512, 8))):
-            kw = dict(mode="async", R_ratio=0.8, rerank=True, persistent=True)
+        # the cheapest points of the merge-trigger sweep (`--workload adaptive`) at each target
+        for tgt, (L, M, Rr) in ((0.9, (128, 4, 0.8)), (0.99, (256, 4, 0.9))):
+            kw = dict(mode="async", R_ratio=Rr, rerank=True, persistent=True)
             st = torch.empty((nq, 8), dtype=torch.int64, device="cuda")
             ids, _ = ix16.search(q, K, L, M, stats=st, **kw)
             times = event_time(torch, lambda: ix16.search(q, K, L, M, **kw), 3, 1, flush)
             t = max_over_ranks(torch, dist, float(np.mean(times)))
             sn = st.cpu().numpy()
-            async_pts[str(tgt)] = {"L": L, "M": M, "R": 0.8, "recall": recall_at_k(ids.cpu().numpy(), gt),
+            async_pts[str(tgt)] = {"L": L, "M": M, "R": Rr, "recall": recall_at_k(ids.cpu().numpy(), gt),
                                    "qps": nq * world / t, "evals_per_query": float(sn[:, 2].mean()),
                                    "merges_per_query": float(sn[:, 5].mean())}
 
