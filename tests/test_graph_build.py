@@ -46,3 +46,19 @@ def test_reachable_matches_scipy_bfs(small_set):
 def test_medoid_matches_the_workload_entry_point(small_set):
     x, _, _ = small_set
     assert graph.medoid(torch.from_numpy(x)) == synth.entry_point(x)
+
+
+def test_repair_with_the_device_bfs_equals_the_repair_with_scipy(small_set):
+    """The large-set builder repairs reachability through synth's repair loop
+    with its own BFS: the same links as with scipy's BFS, and afterwards
+    every vertex is reachable."""
+    x, ids, _ = small_set
+    adj = synth.reverse_fill(x, ids[:, :3], 4)
+    adj[::7, :] = -1                      # cut many vertices off
+    entry = synth.entry_point(x)
+    a1, n1 = synth.repair_reachability(adj, entry, None, x, device="cpu")
+    a2, n2 = synth.repair_reachability(adj, entry, None, x, device="cpu",
+                                       reach=lambda A, e: graph.reachable(torch.from_numpy(A), e))
+    assert n1 == n2 > 0
+    np.testing.assert_array_equal(a1, a2)
+    assert synth.reachable_from(a2, entry).all()
