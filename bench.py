@@ -64,6 +64,8 @@ def parse():
                     help="skip the neighbour-grouping, precision, batching and 10M serving legs of the default run")
     ap.add_argument("--legs-budget-s", type=float, default=780.0,
                     help="the default run's extra legs start only while the run is younger than this")
+    ap.add_argument("--serve-streams", type=int, default=8, help="server groups (launches in flight)")
+    ap.add_argument("--serve-batch", type=int, default=256, help="requests per server launch at most")
     ap.add_argument("--serve-n", type=int, default=SERVE_N,
                     help="point-set size of the serving workload (default 10M)")
     ap.add_argument("--kernel-digest", action="store_true",
@@ -1064,7 +1066,7 @@ def serve_graph(base, log_fn=None):
     return adj, entry, added, t
 
 
-def serve_leg(torch, n=SERVE_N, nreq=20_000):
+def serve_leg(torch, n=SERVE_N, nreq=20_000, args_streams=8, args_batch=256):
     """Continuous-batching server under Poisson arrivals: n x 96 BF16 unit
     vectors (inner product) on a GPU-built degree-32 graph, k in {10, 100},
     recall targets 0.9 / 0.99 mapped to (L, M) on 2,000 calibration queries
@@ -1107,7 +1109,7 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
     LL = np.array([pts[int(k_)][float(t_)][0] for k_, t_ in zip(ks, tg)], np.int32)
     MM = np.array([pts[int(k_)][float(t_)][1] for k_, t_ in zip(ks, tg)], np.int32)
     bytes_per_req = float(np.mean([cost[(int(k_), float(t_))] for k_, t_ in zip(ks, tg)]))
-    cfg = _abi.ServeConfig(max_batch=512, streams=4, max_k=100, max_L=int(LL.max()), max_M=16)
+    cfg = _abi.ServeConfig(max_batch=args_batch, streams=args_streams, max_k=100, max_L=int(LL.max()), max_M=16)
 
     def run(rate):
         """One pass of the trace through a fresh server, driven from native threads (ann_serve_replay):
@@ -1152,7 +1154,8 @@ def serve_leg(torch, n=SERVE_N, nreq=20_000):
 
 def run_serve(args):
     import torch
-    print(json.dumps(serve_leg(torch, n=args.serve_n)))
+    print(json.dumps(serve_leg(torch, n=args.serve_n, args_streams=args.serve_streams,
+                               args_batch=args.serve_batch)))
 
 
 T_START = time.time()
